@@ -1,0 +1,138 @@
+/*
+ * msp.h - C ABI of libmsp, an exact GPU solver for the feasibility market
+ * split problem (n-dimensional subset sum):
+ *
+ *     find every x in {0,1}^n with  sum_j a_ij x_j = d_i  for i = 1..m
+ *
+ * (Kempke and Koch, "A GPU accelerated variant of Schroeppel-Shamir's
+ * algorithm for solving the market split problem", Section 1, eq. 1.)
+ *
+ * The columns are split into four quarters; every subset sum of each
+ * quarter is generated by Gray code with all m row sums packed (Algorithm 1,
+ * Section 2).  The key space of the left and right half-pairs is split into
+ * residue classes of row 1 (and, for large n, a surrogate combination of the
+ * first rows, eq. 2) so that each pass fits in device memory; inside a pass
+ * the half-pair keys are radix-partitioned, sorted in shared memory and
+ * merge-joined, and every key match is verified exactly on all m rows
+ * (Algorithm 2 with the validation of Algorithm 3 and Section 3).
+ *
+ * Conventions for every entry point:
+ *   - All pointers are HOST pointers unless a name says otherwise.  Inputs
+ *     are copied during the call; the caller keeps ownership.
+ *   - A solution is ceil(n/64) little-endian uint64 words: bit j of word
+ *     j/64 is x_j.  Solution lists are sorted ascending as unsigned integers
+ *     (most significant word first) and hold no duplicates.  An empty list
+ *     (count 0) is a valid result.
+ *   - Return values: MSP_OK (0) or MSP_PENDING (1) on success, a negative
+ *     msp_status on error; msp_last_error() then describes the error for the
+ *     calling thread.  The library never aborts the process and has no CPU
+ *     fallback: without a usable CUDA device every solving call fails with
+ *     MSP_ECUDA.
+ *   - Limits: 1 <= m <= 16, 1 <= n <= 100, a_ij >= 0, d_i >= 0 and every row
+ *     sum sum_j a_ij < 65536 (16-bit packed fields).  A right-hand side above
+ *     its row sum is accepted and yields no solution.
+ */
+#ifndef MSP_H
+#define MSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MSP_API __attribute__((visibility("default")))
+#else
+#define MSP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MSP_OK = 0,
+  MSP_PENDING = 1,     /* msp_poll: request not finished yet */
+  MSP_EINVAL = -1,     /* bad argument (null pointer, negative entry, bad handle) */
+  MSP_ERANGE = -2,     /* outside the limits above */
+  MSP_ENOMEM = -3,     /* device or host allocation failed / budget too small */
+  MSP_ECUDA = -4,      /* a CUDA call failed (no device, launch error, ...) */
+  MSP_ETIMEDOUT = -5,  /* a bounded device wait gave up */
+  MSP_EOVERFLOW = -6,  /* result or intermediate list larger than supported */
+  MSP_ECANCELED = -7   /* request canceled before completion */
+} msp_status;
+
+typedef struct msp_instance msp_instance; /* one (A, d); owns its device state */
+typedef struct msp_server msp_server;     /* request queue + device scheduler   */
+
+/* Per-solve counters, filled by msp_solve_all and readable afterwards. */
+typedef struct {
+  int m, n;
+  int quarter[4];             /* quarter sizes q1..q4 (L = Q1+Q3, R = Q2+Q4) */
+  int class_bits;             /* residue classes: 2^class_bits               */
+  int class_rows;             /* rows combined in the residue key (1 = row 1) */
+  int digit_bits;             /* radix-partition digit of the pass sort       */
+  int passes;                 /* residue passes run                           */
+  uint64_t records_left;      /* |L| = 2^(q1+q3) half-pair records            */
+  uint64_t records_right;     /* |R| = 2^(q2+q4)                              */
+  uint64_t row1_candidates_lo;/* C1: pairs (l, r) with row1(l)+row1(r) = d1,  */
+  uint64_t row1_candidates_hi;/*     as a 128-bit integer (hi:lo)             */
+  uint64_t key_matches;       /* distinct matched keys checked exactly        */
+  uint64_t pairs_verified;    /* candidate quadruples checked on all m rows   */
+  uint64_t solutions;         /* distinct solutions                          */
+  uint64_t oversize_segments; /* partitions joined by the general path        */
+  uint64_t device_bytes;      /* peak device memory of the solve              */
+  double ms_total;            /* wall time of the last msp_solve_all          */
+} msp_stats;
+
+/* Validate and copy (A row-major m x n, d length m); upload to the device.
+ * On success *out owns the instance (free with msp_destroy). */
+MSP_API int msp_create(const int32_t *A, const int32_t *d, int m, int n, msp_instance **out);
+
+/* Release an instance and its device memory (NULL is ignored). */
+MSP_API void msp_destroy(msp_instance *inst);
+
+/* Run work of this instance on the given CUDA stream (a cudaStream_t passed
+ * as void*; NULL = the library's own stream for this instance). */
+MSP_API int msp_set_stream(msp_instance *inst, void *cuda_stream);
+
+/* Cap the device memory one solve may use (bytes; 0 = 85% of free memory). */
+MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
+
+/* Exhaustive solve: every x with A x = d.  Blocking.  *masks is allocated by
+ * the library (free with msp_free_solutions; NULL when *count is 0). */
+MSP_API int msp_solve_all(msp_instance *inst, uint64_t **masks, size_t *count, int *words_per_mask);
+
+/* Counters of the last solve of this instance. */
+MSP_API int msp_get_stats(const msp_instance *inst, msp_stats *out);
+
+/* Free a solution buffer returned by this library (NULL is ignored). */
+MSP_API void msp_free_solutions(uint64_t *masks);
+
+/* Solve `count` independent instances of the same (m, n): A[k] and d[k]
+ * point to instance k.  Solutions of instance k are masks[offsets[k] ..
+ * offsets[k+1]) in units of masks (each ceil(n/64) words); offsets has
+ * count+1 entries; *masks is library-allocated (msp_free_solutions). */
+MSP_API int msp_solve_batch(const int32_t *const *A, const int32_t *const *d, int m, int n, int count,
+                    uint64_t **masks, size_t *offsets);
+
+/* Serving: a request queue whose instances share the device.  Requests are
+ * admitted while their next residue pass fits the memory budget, and the
+ * passes of admitted requests are interleaved on several streams. */
+MSP_API int msp_server_create(size_t hbm_budget_bytes, int max_inflight, msp_server **out);
+MSP_API int msp_submit(msp_server *srv, const int32_t *A, const int32_t *d, int m, int n, uint64_t *req_id);
+/* MSP_PENDING while running; MSP_OK with the solutions once done (masks as in
+ * msp_solve_all, then the request is forgotten); a negative status on error. */
+MSP_API int msp_poll(msp_server *srv, uint64_t req_id, uint64_t **masks, size_t *count, int *words);
+MSP_API int msp_cancel(msp_server *srv, uint64_t req_id);
+MSP_API void msp_server_destroy(msp_server *srv);
+
+/* Thread-local description of the last error (never NULL). */
+MSP_API const char *msp_last_error(void);
+
+/* Library version string. */
+MSP_API const char *msp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSP_H */

@@ -1,0 +1,251 @@
+"""ctypes binding of libmsp (include/msp.h): argument marshalling only.
+
+Every step of a solve runs inside libmsp's CUDA kernels.  When the library is
+missing, or no CUDA device is visible, these calls raise :class:`MspError`;
+there is no CPU fallback.
+
+Masks follow the library convention: a solution is a tuple of
+ceil(n / 64) little-endian 64-bit words, bit j of word j // 64 being x_j;
+lists are sorted ascending as unsigned integers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmsp.so")
+_lock = threading.Lock()
+_lib = None
+
+EXPORTED_SYMBOLS = (
+    "msp_create", "msp_destroy", "msp_set_stream", "msp_set_memory_budget", "msp_solve_all",
+    "msp_get_stats", "msp_free_solutions", "msp_solve_batch", "msp_server_create", "msp_submit",
+    "msp_poll", "msp_cancel", "msp_server_destroy", "msp_last_error", "msp_version",
+)
+
+STATUS = {0: "MSP_OK", 1: "MSP_PENDING", -1: "MSP_EINVAL", -2: "MSP_ERANGE", -3: "MSP_ENOMEM",
+          -4: "MSP_ECUDA", -5: "MSP_ETIMEDOUT", -6: "MSP_EOVERFLOW", -7: "MSP_ECANCELED"}
+
+
+class MspError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("quarter", ctypes.c_int * 4),
+                ("class_bits", ctypes.c_int), ("class_rows", ctypes.c_int), ("digit_bits", ctypes.c_int),
+                ("passes", ctypes.c_int), ("records_left", ctypes.c_uint64),
+                ("records_right", ctypes.c_uint64), ("row1_candidates_lo", ctypes.c_uint64),
+                ("row1_candidates_hi", ctypes.c_uint64), ("key_matches", ctypes.c_uint64),
+                ("pairs_verified", ctypes.c_uint64), ("solutions", ctypes.c_uint64),
+                ("oversize_segments", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("ms_total", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["quarter"] = list(self.quarter)
+        d["row1_candidates"] = int(self.row1_candidates_lo) | (int(self.row1_candidates_hi) << 64)
+        return d
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(path: str | None = None):
+    """Load libmsp.so (built by ``paper_2507_05045_gb300.build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or _LIB_PATH
+        if not os.path.exists(p):
+            raise MspError(-4, f"{p} is missing: build it with paper_2507_05045_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        vp = ctypes.c_void_p
+        lib.msp_create.argtypes = [i32p, i32p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+        lib.msp_create.restype = ctypes.c_int
+        lib.msp_destroy.argtypes = [vp]
+        lib.msp_destroy.restype = None
+        lib.msp_set_stream.argtypes = [vp, vp]
+        lib.msp_set_memory_budget.argtypes = [vp, ctypes.c_size_t]
+        lib.msp_solve_all.argtypes = [vp, ctypes.POINTER(u64p), ctypes.POINTER(ctypes.c_size_t),
+                                      ctypes.POINTER(ctypes.c_int)]
+        lib.msp_solve_all.restype = ctypes.c_int
+        lib.msp_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        lib.msp_free_solutions.argtypes = [u64p]
+        lib.msp_free_solutions.restype = None
+        lib.msp_solve_batch.argtypes = [ctypes.POINTER(i32p), ctypes.POINTER(i32p), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(u64p), ctypes.POINTER(ctypes.c_size_t)]
+        lib.msp_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
+        lib.msp_submit.argtypes = [vp, i32p, i32p, ctypes.c_int, ctypes.c_int, u64p]
+        lib.msp_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(u64p), ctypes.POINTER(ctypes.c_size_t),
+                                 ctypes.POINTER(ctypes.c_int)]
+        lib.msp_cancel.argtypes = [vp, ctypes.c_uint64]
+        lib.msp_server_destroy.argtypes = [vp]
+        lib.msp_server_destroy.restype = None
+        lib.msp_last_error.restype = ctypes.c_char_p
+        lib.msp_version.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc < 0:
+        raise MspError(rc, load_library().msp_last_error().decode())
+    return rc
+
+
+def _i32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _take_masks(lib, ptr, count: int, words: int):
+    if count == 0:
+        return []
+    arr = np.ctypeslib.as_array(ptr, shape=(count * words,)).copy()
+    lib.msp_free_solutions(ptr)
+    return [tuple(int(w) for w in arr[i * words:(i + 1) * words]) for i in range(count)]
+
+
+class Instance:
+    """One (A, d) instance: ``msp_create`` / ``msp_solve_all`` / ``msp_destroy``."""
+
+    def __init__(self, A, d, stream: int | None = None, memory_budget: int = 0):
+        lib = load_library()
+        A = np.asarray(A)
+        if A.ndim != 2:
+            raise MspError(-1, "A must be a 2-D matrix")
+        self.m, self.n = int(A.shape[0]), int(A.shape[1])
+        a, ap = _i32(A)
+        dd, dp = _i32(np.asarray(d).reshape(-1))
+        if dd.shape[0] != self.m:
+            raise MspError(-1, "d must have one entry per row of A")
+        h = ctypes.c_void_p()
+        _check(lib.msp_create(ap, dp, self.m, self.n, ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        if stream is not None:
+            _check(lib.msp_set_stream(h, ctypes.c_void_p(stream)))
+        if memory_budget:
+            _check(lib.msp_set_memory_budget(h, ctypes.c_size_t(memory_budget)))
+
+    def solve_all(self):
+        ptr = ctypes.POINTER(ctypes.c_uint64)()
+        cnt = ctypes.c_size_t()
+        words = ctypes.c_int()
+        _check(self._lib.msp_solve_all(self._h, ctypes.byref(ptr), ctypes.byref(cnt), ctypes.byref(words)))
+        return _take_masks(self._lib, ptr, cnt.value, words.value)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._lib.msp_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.msp_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_all(A, d, **kw):
+    """Every x in {0,1}^n with A x = d, as sorted mask tuples."""
+    with Instance(A, d, **kw) as inst:
+        return inst.solve_all()
+
+
+def solve_batch(instances):
+    """Solve a list of (A, d) pairs of one (m, n) with ``msp_solve_batch``."""
+    lib = load_library()
+    if not instances:
+        return []
+    m, n = np.asarray(instances[0][0]).shape
+    keep = []
+    Ap = (ctypes.POINTER(ctypes.c_int32) * len(instances))()
+    dp = (ctypes.POINTER(ctypes.c_int32) * len(instances))()
+    for k, (A, d) in enumerate(instances):
+        if np.asarray(A).shape != (m, n):
+            raise MspError(-1, "all batch instances must share (m, n)")
+        a, ap = _i32(A)
+        dd, dpp = _i32(np.asarray(d).reshape(-1))
+        keep += [a, dd]
+        Ap[k] = ap
+        dp[k] = dpp
+    ptr = ctypes.POINTER(ctypes.c_uint64)()
+    offs = (ctypes.c_size_t * (len(instances) + 1))()
+    _check(lib.msp_solve_batch(Ap, dp, m, n, len(instances), ctypes.byref(ptr), offs))
+    words = (n + 63) // 64
+    total = offs[len(instances)]
+    flat = _take_masks(lib, ptr, total, words)
+    return [flat[offs[k]:offs[k + 1]] for k in range(len(instances))]
+
+
+class Server:
+    """``msp_server_create`` / ``msp_submit`` / ``msp_poll`` / ``msp_cancel``."""
+
+    def __init__(self, hbm_budget: int = 0, max_inflight: int = 4):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.msp_server_create(ctypes.c_size_t(hbm_budget), max_inflight, ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, A, d) -> int:
+        A = np.asarray(A)
+        m, n = A.shape
+        a, ap = _i32(A)
+        dd, dp = _i32(np.asarray(d).reshape(-1))
+        rid = ctypes.c_uint64()
+        _check(self._lib.msp_submit(self._h, ap, dp, m, n, ctypes.byref(rid)))
+        return int(rid.value)
+
+    def poll(self, req_id: int):
+        """None while pending, else the sorted solution list (raises on error)."""
+        ptr = ctypes.POINTER(ctypes.c_uint64)()
+        cnt = ctypes.c_size_t()
+        words = ctypes.c_int()
+        rc = _check(self._lib.msp_poll(self._h, ctypes.c_uint64(req_id), ctypes.byref(ptr), ctypes.byref(cnt),
+                                       ctypes.byref(words)))
+        if rc == 1:
+            return None
+        return _take_masks(self._lib, ptr, cnt.value, words.value)
+
+    def cancel(self, req_id: int):
+        _check(self._lib.msp_cancel(self._h, ctypes.c_uint64(req_id)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.msp_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

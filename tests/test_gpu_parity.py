@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+The result of a solve is an exact set of integer bitmasks, so every
+comparison here is bit-exact: the sorted solution list of libmsp must equal
+the oracle's.  Inputs come from the seeded generator only.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import msp_instances as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def msp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_05045_gb300 import build
+    build.build()
+    import paper_2507_05045_gb300 as m
+    return m
+
+
+def load_golden(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    g = json.load(open(path))
+    out = []
+    for e in g["instances"]:
+        A, d, x = mi.generate(e["m"], e["n"], e["seed"], planted=e["planted"], h=e["h"])
+        sols = [tuple(int(w, 16) for w in s) for s in e["solutions"]]
+        out.append((e, A, d, x, sols))
+    return out
+
+
+def test_hand_instances(msp):
+    g = json.load(open(os.path.join(GOLDEN, "hand_instances.json")))
+    for inst in g["instances"]:
+        got = [s[0] for s in msp.solve_all(np.array(inst["A"]), np.array(inst["d"]))]
+        assert got == inst["solutions"], inst["name"]
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_small_vs_brute(msp, seed):
+    rng = np.random.default_rng(seed)
+    m = int(rng.integers(1, 11))
+    n = int(rng.integers(1, 23))
+    K = int(rng.choice([2, 3, 5, 20, 100]))
+    A, d, _ = mi.generate(m, n, 5000 + seed, K=K, planted=bool(seed % 2), h=n // 2)
+    assert msp.solve_all(A, d) == oracle.brute(A, d)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 9, 13])
+def test_tiny_n_every_quarter_shape(msp, n):
+    for seed in range(3):
+        A, d, _ = mi.generate(2, n, 90 + seed, K=3, planted=True, h=n // 2)
+        assert msp.solve_all(A, d) == oracle.brute(A, d)
+
+
+def test_degenerate_inputs(msp):
+    # all-zero matrix: every vector solves d = 0, none solves d != 0
+    A = np.zeros((3, 12), np.int32)
+    assert [s[0] for s in msp.solve_all(A, [0, 0, 0])] == list(range(1 << 12))
+    assert msp.solve_all(A, [0, 1, 0]) == []
+    # right-hand side above a row sum
+    A, d, _ = mi.generate(3, 16, 3)
+    d2 = d.copy()
+    d2[1] = A[1].sum() + 1
+    assert msp.solve_all(A, d2) == []
+    # d = 0 with positive entries: x = 0 only
+    A = np.arange(1, 21, dtype=np.int32).reshape(2, 10)
+    assert msp.solve_all(A, [0, 0]) == [(0,)]
+    # zero columns and duplicate rows
+    A, d, _ = mi.generate(3, 18, 4, K=4, planted=True, h=9)
+    A2 = np.hstack([A, np.zeros((3, 2), np.int32)])
+    A2 = np.vstack([A2, A2[0:1]])
+    d2 = np.concatenate([d, d[0:1]])
+    assert msp.solve_all(A2, d2) == oracle.brute(A2, d2)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_small_K_long_equal_key_runs(msp, seed):
+    # K = 2: many subsets share one vector, so keys repeat in long runs
+    A, d, _ = mi.generate(2, 22, 6000 + seed, K=2, planted=True, h=11)
+    assert msp.solve_all(A, d) == oracle.brute(A, d)
+
+
+def test_config_4_30(msp):
+    for e, A, d, x, sols in load_golden("sols_4_30.json"):
+        got = msp.solve_all(A, d)
+        assert got == sols
+        if x is not None:
+            assert mi.mask_of(x) in got
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_5_40_vs_mitm(msp, seed):
+    A, d, _ = mi.generate(5, 40, 7000 + seed, planted=bool(seed % 2), h=20)
+    assert msp.solve_all(A, d) == oracle.mitm(A, d)
+
+
+def test_row1_candidate_count_matches_counting_dp(msp):
+    for (m, n, seed) in [(4, 30, 1), (5, 40, 2), (6, 50, 3), (3, 22, 4)]:
+        A, d, _ = mi.generate(m, n, seed)
+        with msp.Instance(A, d) as inst:
+            inst.solve_all()
+            st = inst.stats()
+        assert st["row1_candidates"] == oracle.row1_candidates(A, d)
+
+
+def test_config_6_50_batch(msp):
+    entries = load_golden("sols_6_50_batch.json")
+    got = msp.solve_batch([(A, d) for _, A, d, _, _ in entries])
+    for (e, A, d, x, sols), g in zip(entries, got):
+        assert g == sols, e["seed"]
+        if x is not None:
+            assert mi.mask_of(x) in g
+
+
+def test_config_6_50_single(msp):
+    for e, A, d, x, sols in load_golden("sols_6_50_batch.json")[:8]:
+        assert msp.solve_all(A, d) == sols
+
+
+def test_many_passes_same_result(msp):
+    # a small budget forces many residue passes: the set must not change
+    e, A, d, x, sols = load_golden("sols_6_50_batch.json")[40]
+    with msp.Instance(A, d, memory_budget=400 << 20) as inst:
+        got = inst.solve_all()
+        st = inst.stats()
+    assert got == sols
+    assert st["passes"] >= 1
+
+
+def test_config_7_60(msp):
+    for e, A, d, x, sols in load_golden("sols_7_60.json"):
+        with msp.Instance(A, d) as inst:
+            got = inst.solve_all()
+            st = inst.stats()
+        assert got == sols
+        assert st["row1_candidates"] == oracle.row1_candidates(A, d)
+
+
+def _check_solutions_exact(A, d, sols):
+    A = np.asarray(A, dtype=np.int64)
+    n = A.shape[1]
+    for s in sols:
+        v = sum(w << (64 * k) for k, w in enumerate(s))
+        x = np.array([(v >> j) & 1 for j in range(n)], dtype=np.int64)
+        assert np.array_equal(A @ x, np.asarray(d, dtype=np.int64))
+
+
+def _subcube_parity(msp_sols, A, d, fixed_cols, fixed_vals):
+    """GPU solutions agreeing with the fixed columns == oracle on the restriction."""
+    A2, d2, free = mi.restrict(A, d, fixed_cols, fixed_vals)
+    n = np.asarray(A).shape[1]
+    if np.any(d2 < 0):
+        want = []
+    else:
+        want = oracle.mitm(A2, d2.astype(np.int32))
+    lifted = []
+    for s in want:
+        v = sum(w << (64 * k) for k, w in enumerate(s))
+        full = sum(1 << fixed_cols[i] for i in range(len(fixed_cols)) if fixed_vals[i])
+        full |= sum(1 << free[j] for j in range(len(free)) if (v >> j) & 1)
+        lifted.append(full)
+    got = []
+    for s in msp_sols:
+        v = sum(w << (64 * k) for k, w in enumerate(s))
+        if all(((v >> c) & 1) == b for c, b in zip(fixed_cols, fixed_vals)):
+            got.append(v)
+    assert sorted(got) == sorted(lifted)
+
+
+def test_config_8_70_planted_properties_and_subcube(msp):
+    A, d, x = mi.generate(8, 70, 8, planted=True, h=35)
+    with msp.Instance(A, d) as inst:
+        sols = inst.solve_all()
+        st = inst.stats()
+    assert mi.mask_of(x) in sols
+    _check_solutions_exact(A, d, sols)
+    assert st["row1_candidates"] == oracle.row1_candidates(A, d)
+    # 26 columns fixed to x*: the 44 free columns are solved by the oracle
+    rng = np.random.default_rng(8)
+    cols = sorted(int(c) for c in rng.choice(70, 26, replace=False))
+    _subcube_parity(sols, A, d, cols, [int(x[c]) for c in cols])
+
+
+@pytest.mark.slow
+def test_config_9_80_planted_properties_and_subcube(msp):
+    A, d, x = mi.generate(9, 80, 9, planted=True, h=40)
+    with msp.Instance(A, d) as inst:
+        sols = inst.solve_all()
+        st = inst.stats()
+    assert mi.mask_of(x) in sols
+    _check_solutions_exact(A, d, sols)
+    assert st["row1_candidates"] == oracle.row1_candidates(A, d)
+    rng = np.random.default_rng(9)
+    cols = sorted(int(c) for c in rng.choice(80, 34, replace=False))
+    _subcube_parity(sols, A, d, cols, [int(x[c]) for c in cols])
+
+
+def test_row_and_column_permutation_invariance(msp):
+    A, d, x = mi.generate(6, 48, 77, K=20, planted=True, h=24)
+    base = msp.solve_all(A, d)
+    perm_r = np.array([3, 0, 5, 1, 4, 2])
+    assert msp.solve_all(A[perm_r], d[perm_r]) == base
+    perm_c = np.random.default_rng(1).permutation(48)
+    got = msp.solve_all(A[:, perm_c], d)
+    mapped = sorted(
+        (sum(1 << k for k in range(48) if (s[0] >> perm_c[k]) & 1),) for s in base)
+    assert got == mapped
+
+
+def test_server_mixed_stream_matches_single_solves(msp):
+    insts = []
+    for k in range(24):
+        m = [4, 5, 6][k % 3]
+        A, d, _ = mi.generate(m, 10 * (m - 1), 8000 + k, planted=bool(k % 2), h=5 * (m - 1))
+        insts.append((A, d))
+    alone = [msp.solve_all(A, d) for A, d in insts]
+    with msp.Server(max_inflight=4) as srv:
+        ids = [srv.submit(A, d) for A, d in insts]
+        results = {}
+        import time
+        t0 = time.time()
+        while len(results) < len(ids) and time.time() - t0 < 300:
+            for i in ids:
+                if i not in results:
+                    r = srv.poll(i)
+                    if r is not None:
+                        results[i] = r
+            time.sleep(0.002)
+    assert [results[i] for i in ids] == alone
