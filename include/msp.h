@@ -81,7 +81,32 @@ typedef struct {
   uint64_t oversize_segments; /* partitions joined by the general path        */
   uint64_t device_bytes;      /* peak device memory of the solve              */
   double ms_total;            /* wall time of the last msp_solve_all          */
+  uint64_t kernel_launches;   /* kernels launched by the last solve           */
+  uint64_t fast_passes_redone;/* streaming passes re-run on the exact path    */
+  uint64_t h2d_bytes;         /* host-to-device bytes copied by the solve     */
+  uint64_t d2h_bytes;         /* device-to-host bytes copied by the solve     */
+  /* Filled only when profiling is on (msp_set_profiling): per kernel kind
+   * (MSP_K_* below) the summed CUDA-event time, the launches, and the
+   * algorithmic device-memory bytes (records written / read x 8 bytes). */
+  double kernel_ms[12];
+  uint64_t kernel_count[12];
+  uint64_t kernel_bytes[12];
 } msp_stats;
+
+/* Kernel kinds indexing msp_stats.kernel_* */
+enum {
+  MSP_K_GRAY = 0,      /* quarter lists by Gray code                 */
+  MSP_K_BUCKET = 1,    /* residue-class counting sort                */
+  MSP_K_C1 = 2,        /* row-1 candidate count                      */
+  MSP_K_GEN_COUNT = 3, /* partition histograms of a pass             */
+  MSP_K_OFFSETS = 4,   /* histograms to offsets                      */
+  MSP_K_GEN_SCATTER = 5, /* records generated and radix-partitioned  */
+  MSP_K_JOIN = 6,      /* shared-memory sort + merge-join            */
+  MSP_K_JOIN_BIG = 7,  /* oversize partitions                        */
+  MSP_K_RECOVER = 8,   /* quarter elements behind matched keys       */
+  MSP_K_VERIFY = 9,    /* exact all-row check                        */
+  MSP_K_OTHER = 10
+};
 
 /* Validate and copy (A row-major m x n, d length m); upload to the device.
  * On success *out owns the instance (free with msp_destroy). */
@@ -96,6 +121,17 @@ MSP_API int msp_set_stream(msp_instance *inst, void *cuda_stream);
 
 /* Cap the device memory one solve may use (bytes; 0 = 85% of free memory). */
 MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
+
+/* Instance options (msp_set_option):
+ *   MSP_OPT_EXACT_PATH  1 = skip the streaming pass and run every residue
+ *                       pass on the exact two-phase path (count, then
+ *                       scatter); 0 = default (streaming, exact re-run of
+ *                       any pass whose partitions overflow). */
+enum { MSP_OPT_EXACT_PATH = 1 };
+MSP_API int msp_set_option(msp_instance *inst, int option, int64_t value);
+
+/* Time every kernel launch of later solves with CUDA events (on = 1). */
+MSP_API int msp_set_profiling(msp_instance *inst, int on);
 
 /* Exhaustive solve: every x with A x = d.  Blocking.  *masks is allocated by
  * the library (free with msp_free_solutions; NULL when *count is 0). */

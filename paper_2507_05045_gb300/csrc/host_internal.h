@@ -19,6 +19,8 @@ struct msp_instance {
   size_t budget = 0;
   msp_stats stats{};
   int device = 0;
+  bool profiling = false;
+  bool force_exact = false;
 };
 
 namespace msp {

@@ -102,6 +102,32 @@ struct PassDev {
   uint32_t big_cap;
 };
 
+// Streaming pass (fastpath.cu): partitions of fixed capacity <= kFastCap.
+constexpr int kFastCap = 4864;
+
+struct FastPass {
+  SideGen side[2];
+  uint32_t cmask;
+  int c0, nclass;
+  int D, S;
+  const uint64_t *class_base[2];  // [nclass] first record of the class region
+  const uint32_t *cap[2];         // [nclass] records per partition (multiple of 16)
+  uint32_t *fill[2];              // [nclass][2^D] records appended (zeroed per pass)
+  uint64_t *rec[2];
+  unsigned int *overflow;         // this pass dropped a record (partition full)
+  unsigned int *error;            // a bounded wait gave up
+  uint64_t *match_key;
+  uint32_t *match_cls;
+  unsigned long long *match_count;
+  uint64_t match_cap;
+};
+cudaError_t launch_class_sizes(const uint32_t *offO, const uint32_t *offI, uint32_t M, unsigned long long *out,
+                               cudaStream_t s);
+cudaError_t launch_scatter_fast(const FastPass &p, int nclass_run, cudaStream_t s);
+cudaError_t launch_join_fast(const FastPass &p, int nclass_run, cudaStream_t s);
+size_t scatter_fast_smem(int D);
+size_t join_fast_smem(int S);
+
 constexpr int kJoinCap = 6144;   // records per side held in shared memory
 constexpr int kJoinThreads = 512;
 constexpr int kGenThreads = 256;

@@ -57,8 +57,9 @@ Plan make_plan(int m, int n) {
   p.lgL = p.q[0] + p.q[2];
   p.lgR = p.q[1] + p.q[3];
   const int lgmax = std::max(p.lgL, p.lgR);
-  // about 2^23 records per class and side; partitions of about 2^12.
-  p.B = std::min(22, std::max(0, lgmax - 23));
+  // about 2^22 records per class and side, partitions of about 2^12
+  // (1024 digits); the exact class-size convolution needs 2^B <= 2^18.
+  p.B = std::min(18, std::max(0, lgmax - 22));
   p.t = p.B <= 8 ? 1 : (p.B <= 14 ? 2 : 3);
   p.t = std::min(p.t, m);
   p.D = std::min(12, std::max(0, lgmax - p.B - 12));
@@ -118,6 +119,69 @@ struct DevAlloc {
       return fail(e_ == cudaErrorMemoryAllocation ? MSP_ENOMEM : MSP_ECUDA,           \
                   std::string(#call) + ": " + cudaGetErrorString(e_));                \
     }                                                                                 \
+  } while (0)
+
+// Per-launch CUDA-event timing (only when the instance has profiling on)
+// and launch counting (always).
+struct Prof {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  msp_stats *st = nullptr;
+  struct Item {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Item> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  cudaEvent_t a_ = nullptr;
+  void begin() {
+    if (!on) return;
+    a_ = get();
+    cudaEventRecord(a_, s);
+  }
+  void end(int kind, int kernels, uint64_t bytes) {
+    st->kernel_launches += kernels;
+    if (!on) return;
+    cudaEvent_t b = get();
+    cudaEventRecord(b, s);
+    pending.push_back({kind, a_, b});
+    st->kernel_count[kind] += kernels;
+    st->kernel_bytes[kind] += bytes;
+  }
+  // call after the stream reached the recorded events
+  void flush() {
+    for (auto &it : pending) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, it.a, it.b) == cudaSuccess) st->kernel_ms[it.kind] += ms;
+      pool.push_back(it.a);
+      pool.push_back(it.b);
+    }
+    pending.clear();
+  }
+  ~Prof() {
+    for (auto &it : pending) {
+      cudaEventDestroy(it.a);
+      cudaEventDestroy(it.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+#define LAUNCH(kind, kernels, bytes, call) \
+  do {                                     \
+    prof.begin();                          \
+    CK(call);                              \
+    prof.end(kind, kernels, bytes);        \
   } while (0)
 
 int validate(const int32_t *A, const int32_t *d, int m, int n) {
@@ -212,15 +276,27 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
   const uint32_t M = 1u << p.B;
   const uint32_t cmask = M - 1u;
 
+  Prof prof;
+  prof.on = inst->profiling;
+  prof.s = s;
+  prof.st = &st;
+  auto h2d = [&](void *dst, const void *hsrc, size_t b) {
+    st.h2d_bytes += b;
+    return cudaMemcpyAsync(dst, hsrc, b, cudaMemcpyHostToDevice, s);
+  };
+  auto d2h = [&](void *hdst, const void *dsrc, size_t b) {
+    st.d2h_bytes += b;
+    return cudaMemcpyAsync(hdst, dsrc, b, cudaMemcpyDeviceToHost, s);
+  };
   DevAlloc da(s);
   uint64_t *d_pcol, *d_kcol;
   uint32_t *d_ccol;
   CK(da.get(&d_pcol, pcol.size()));
   CK(da.get(&d_kcol, kcol.size()));
   CK(da.get(&d_ccol, ccol.size()));
-  CK(cudaMemcpyAsync(d_pcol, pcol.data(), pcol.size() * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(d_kcol, kcol.data(), kcol.size() * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(d_ccol, ccol.data(), ccol.size() * 4, cudaMemcpyHostToDevice, s));
+  CK(h2d(d_pcol, pcol.data(), pcol.size() * 8));
+  CK(h2d(d_kcol, kcol.data(), kcol.size() * 8));
+  CK(h2d(d_ccol, ccol.data(), ccol.size() * 4));
 
   // ---- S1: quarter lists ----
   QuarterDev qd[4];
@@ -231,7 +307,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     CK(da.get(&qd[k].key, qd[k].size));
     CK(da.get(&qd[k].cls, qd[k].size));
     CK(da.get(&qd[k].v1, qd[k].size));
-    CK(launch_gray(ic, d_pcol, d_kcol, d_ccol, qd[k], p.col0[k], s));
+    LAUNCH(MSP_K_GRAY, 1, 0, launch_gray(ic, d_pcol, d_kcol, d_ccol, qd[k], p.col0[k], s));
   }
 
   // ---- S2: bucket the four lists by (transformed) class ----
@@ -253,10 +329,10 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     CK(da.get(&bd[l].idx, q.size));
     CK(da.get(&bd[l].off, (size_t)M + 1));
     CK(cudaMemsetAsync(d_hist, 0, sizeof(uint32_t) * M, s));
-    CK(launch_count_classes(q.cls, q.size, static_cast<uint32_t>(mul[l]), cadd[l], cmask, d_hist, s));
-    CK(launch_scan_u32(d_hist, bd[l].off, M, d_scantmp, s));
+    LAUNCH(MSP_K_BUCKET, 1, 0, launch_count_classes(q.cls, q.size, static_cast<uint32_t>(mul[l]), cadd[l], cmask, d_hist, s));
+    LAUNCH(MSP_K_BUCKET, 3, 0, launch_scan_u32(d_hist, bd[l].off, M, d_scantmp, s));
     CK(cudaMemcpyAsync(d_cursor, bd[l].off, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, s));
-    CK(launch_bucket_scatter(q, mul[l], kadd[l], cadd[l], cmask, d_cursor, bd[l], s));
+    LAUNCH(MSP_K_BUCKET, 1, 0, launch_bucket_scatter(q, mul[l], kadd[l], cadd[l], cmask, d_cursor, bd[l], s));
   }
 
   // ---- row-1 candidate count C1 (the metric's unit of work) ----
@@ -272,29 +348,26 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
       const int len = (k == 0 || k == 2) ? len13 : len24;
       CK(da.get(&h[k], len));
       CK(cudaMemsetAsync(h[k], 0, sizeof(unsigned long long) * len, s));
-      CK(launch_v1_hist(qd[k].v1, qd[k].size, h[k], s));
+      LAUNCH(MSP_K_C1, 1, 0, launch_v1_hist(qd[k].v1, qd[k].size, h[k], s));
     }
     CK(da.get(&hl, lenl));
     CK(da.get(&hr, lenr));
     CK(da.get(&c1, 2));
-    CK(launch_row1_candidates(h[0], h[2], len13, h[1], h[3], len24, hl, hr, lenl, lenr, inst->d[0], c1, s));
+    LAUNCH(MSP_K_C1, 3, 0, launch_row1_candidates(h[0], h[2], len13, h[1], h[3], len24, hl, hr, lenl, lenr, inst->d[0], c1, s));
     unsigned long long c1h[2];
-    CK(cudaMemcpyAsync(c1h, c1, sizeof(c1h), cudaMemcpyDeviceToHost, s));
+    CK(d2h(c1h, c1, sizeof(c1h)));
     CK(cudaStreamSynchronize(s));
     st.row1_candidates_lo = c1h[0];
     st.row1_candidates_hi = c1h[1];
   }
 
   // ---- pass setup ----
-  PassDev pd{};
-  pd.cmask = cmask;
-  pd.D = p.D;
-  pd.S = p.S;
   const int nd = 1 << p.D;
+  SideGen gens[2];
   for (int side = 0; side < 2; ++side) {
     const BucketDev &o = bd[side == 0 ? 0 : 2];
     const BucketDev &in = bd[side == 0 ? 1 : 3];
-    SideGen &g = pd.side[side];
+    SideGen &g = gens[side];
     g.okey = o.key;
     g.ocls = o.cls;
     g.osize = o.size;
@@ -308,113 +381,276 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
   size_t free_b = 0, total_b = 0;
   CK(cudaMemGetInfo(&free_b, &total_b));
   size_t budget = inst->budget ? inst->budget : static_cast<size_t>(0.85 * free_b);
-  budget = std::min(budget, static_cast<size_t>(0.92 * free_b));
-  const double est_class[2] = {std::ldexp(1.0, p.lgL - p.B), std::ldexp(1.0, p.lgR - p.B)};
-  const size_t per_class_meta =
-      (size_t)nd * (sizeof(uint64_t) + sizeof(uint32_t)) * 2 +
-      (size_t)nd * sizeof(uint32_t) * (pd.side[0].slices + pd.side[1].slices) + 64;
-  const double per_class_bytes = (est_class[0] + est_class[1]) * 8.0 * 1.08 + per_class_meta;
-  const size_t fixed_reserve = (size_t)64 << 20;  // matches, lists of oversize partitions
-  if (budget < fixed_reserve + per_class_bytes)
-    return fail(MSP_ENOMEM, "memory budget too small for one residue class");
-  int max_classes = static_cast<int>(std::min<double>(
-      M, std::floor((double)(budget - fixed_reserve) / per_class_bytes)));
-  max_classes = std::max(1, std::min(max_classes, 1 << 16));
-  uint64_t rec_cap[2] = {
-      static_cast<uint64_t>(std::min<double>(std::ldexp(1.0, p.lgL), est_class[0] * 1.08 * max_classes + 4096)),
-      static_cast<uint64_t>(std::min<double>(std::ldexp(1.0, p.lgR), est_class[1] * 1.08 * max_classes + 4096))};
-  for (int side = 0; side < 2; ++side) {
-    CK(da.get(&pd.cnt[side], (size_t)max_classes * pd.side[side].slices * nd));
-    CK(da.get(&pd.segstart[side], (size_t)max_classes * nd));
-    CK(da.get(&pd.seglen[side], (size_t)max_classes * nd));
-    CK(da.get(&pd.classtot[side], (size_t)max_classes));
-    CK(da.get(&pd.classbase[side], (size_t)max_classes));
-    CK(da.get(&pd.rec[side], rec_cap[side]));
-  }
-  pd.match_cap = 1u << 20;
-  CK(da.get(&pd.match_key, pd.match_cap));
-  CK(da.get(&pd.match_cls, pd.match_cap));
-  CK(da.get(&pd.match_count, 1));
-  CK(cudaMemsetAsync(pd.match_count, 0, sizeof(unsigned long long), s));
-  pd.big_cap = static_cast<uint32_t>(std::min<uint64_t>((uint64_t)max_classes * nd, 1u << 24));
-  CK(da.get(&pd.big_list, pd.big_cap));
-  CK(da.get(&pd.big_count, 1));
+  budget = std::min(budget, static_cast<size_t>(0.92 * free_b) + da.bytes);
+  const size_t fixed_reserve = (size_t)64 << 20;  // matches and small per-pass tables
 
-  std::vector<uint64_t> tot_h(2 * (size_t)max_classes), base_h(2 * (size_t)max_classes);
-  unsigned int big_h = 0;
-  uint64_t oversize = 0;
+  uint64_t *match_key;
+  uint32_t *match_cls;
+  unsigned long long *match_count;
+  const uint64_t match_cap = 1u << 20;
+  CK(da.get(&match_key, match_cap));
+  CK(da.get(&match_cls, match_cap));
+  CK(da.get(&match_count, 1));
+  CK(cudaMemsetAsync(match_count, 0, sizeof(unsigned long long), s));
+
+  uint64_t *rec[2] = {nullptr, nullptr};
+  uint64_t rec_cap[2] = {0, 0};
+  // (re)allocate the record buffers to hold at least need[] records
+  auto ensure_rec = [&](const uint64_t need[2]) -> cudaError_t {
+    for (int side = 0; side < 2; ++side) {
+      if (need[side] <= rec_cap[side]) continue;
+      if (rec[side]) da.free1(rec[side], sizeof(uint64_t) * rec_cap[side]);
+      rec[side] = nullptr;
+      rec_cap[side] = 0;
+      cudaError_t e = da.get(&rec[side], need[side]);
+      if (e != cudaSuccess) return e;
+      rec_cap[side] = need[side];
+    }
+    return cudaSuccess;
+  };
+
   int passes = 0;
-  for (uint32_t c0 = 0; c0 < M;) {
-    if (inst->cancel && *inst->cancel) return fail(MSP_ECANCELED, "request canceled");
-    pd.c0 = static_cast<int>(c0);
-    pd.nclass = static_cast<int>(std::min<uint64_t>(max_classes, M - c0));
-    CK(launch_gen_count(pd, s));
-    CK(launch_counts_to_offsets(pd, s));
-    CK(cudaMemcpyAsync(tot_h.data(), pd.classtot[0], sizeof(uint64_t) * pd.nclass, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(tot_h.data() + max_classes, pd.classtot[1], sizeof(uint64_t) * pd.nclass,
-                       cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    // the longest prefix of classes that fits both record buffers
-    uint64_t acc[2] = {0, 0};
-    int run = 0;
-    for (int c = 0; c < pd.nclass; ++c) {
-      const uint64_t a0 = tot_h[c], a1 = tot_h[max_classes + c];
-      if (acc[0] + a0 > rec_cap[0] || acc[1] + a1 > rec_cap[1]) break;
-      if (a0 >= (1ull << 31) || a1 >= (1ull << 31)) break;
-      base_h[c] = acc[0];
-      base_h[max_classes + c] = acc[1];
-      acc[0] += a0;
-      acc[1] += a1;
-      ++run;
+  uint64_t oversize = 0;
+  std::vector<std::pair<uint32_t, uint32_t>> exact_ranges;
+  bool fast = !inst->force_exact && M <= (1u << 18);
+  std::vector<unsigned long long> csz[2];
+  std::vector<uint32_t> capv[2];
+  if (fast) {
+    // exact class sizes by convolution of the bucket histograms (S2)
+    unsigned long long *d_csz;
+    CK(da.get(&d_csz, 2 * (size_t)M));
+    LAUNCH(MSP_K_OTHER, 1, 0, launch_class_sizes(bd[0].off, bd[1].off, M, d_csz, s));
+    LAUNCH(MSP_K_OTHER, 1, 0, launch_class_sizes(bd[2].off, bd[3].off, M, d_csz + M, s));
+    for (int side = 0; side < 2; ++side) {
+      csz[side].resize(M);
+      capv[side].resize(M);
+      CK(d2h(csz[side].data(), d_csz + (size_t)side * M, sizeof(unsigned long long) * M));
     }
-    if (run == 0) {
-      // A class larger than the buffers (skewed class sizes): grow them to
-      // hold it if the budget allows, then retry the pass.
-      const uint64_t need0 = tot_h[0], need1 = tot_h[max_classes];
-      const double need_bytes = 8.0 * (double)(need0 + need1) + (double)da.bytes -
-                                8.0 * (double)(rec_cap[0] + rec_cap[1]);
-      if (need0 >= (1ull << 31) || need1 >= (1ull << 31) || need_bytes > (double)budget)
-        return fail(MSP_ENOMEM, "one residue class does not fit the memory budget");
-      for (int side = 0; side < 2; ++side) {
-        const uint64_t need = side ? need1 : need0;
-        if (need <= rec_cap[side]) continue;
-        da.free1(pd.rec[side], sizeof(uint64_t) * rec_cap[side]);
-        rec_cap[side] = need;
-        CK(da.get(&pd.rec[side], rec_cap[side]));
+    CK(cudaStreamSynchronize(s));
+    prof.flush();
+    for (int side = 0; side < 2 && fast; ++side)
+      for (uint32_t c = 0; c < M; ++c) {
+        const double mean = (double)csz[side][c] / nd;
+        uint64_t cap = static_cast<uint64_t>(std::ceil(mean + 8.0 * std::sqrt(mean) + 32.0));
+        cap = (cap + 15) & ~uint64_t(15);
+        if (cap > (uint64_t)kFastCap) {
+          fast = false;
+          break;
+        }
+        capv[side][c] = static_cast<uint32_t>(cap);
       }
-      continue;
+  }
+  if (fast) {
+    // ---- streaming passes: greedy runs of classes whose partition regions
+    //      fit the record budget ----
+    const double rec_budget = std::max(0.0, (double)budget - (double)da.bytes - (double)fixed_reserve);
+    double tot_region[2] = {0, 0};
+    for (int side = 0; side < 2; ++side)
+      for (uint32_t c = 0; c < M; ++c) tot_region[side] += (double)capv[side][c] * nd;
+    const double frac0 = tot_region[0] / std::max(1.0, tot_region[0] + tot_region[1]);
+    const uint64_t lim[2] = {static_cast<uint64_t>(rec_budget / 8.0 * frac0),
+                             static_cast<uint64_t>(rec_budget / 8.0 * (1.0 - frac0))};
+    const int max_run = 1 << 16;
+    struct PassPlan {
+      uint32_t c0, c1;
+      uint64_t recs;
+    };
+    std::vector<PassPlan> plan;
+    std::vector<uint64_t> base_h[2] = {std::vector<uint64_t>(M), std::vector<uint64_t>(M)};
+    uint64_t need[2] = {0, 0};
+    for (uint32_t c0 = 0; c0 < M;) {
+      uint64_t acc[2] = {0, 0}, recs = 0;
+      uint32_t c = c0;
+      while (c < M && (int)(c - c0) < max_run) {
+        const uint64_t r0 = (uint64_t)capv[0][c] * nd, r1 = (uint64_t)capv[1][c] * nd;
+        if (c > c0 && (acc[0] + r0 > lim[0] || acc[1] + r1 > lim[1])) break;
+        base_h[0][c] = acc[0];
+        base_h[1][c] = acc[1];
+        acc[0] += r0;
+        acc[1] += r1;
+        recs += csz[0][c] + csz[1][c];
+        ++c;
+      }
+      plan.push_back({c0, c, recs});
+      need[0] = std::max(need[0], acc[0]);
+      need[1] = std::max(need[1], acc[1]);
+      c0 = c;
     }
-    CK(cudaMemcpyAsync(pd.classbase[0], base_h.data(), sizeof(uint64_t) * run, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(pd.classbase[1], base_h.data() + max_classes, sizeof(uint64_t) * run,
-                       cudaMemcpyHostToDevice, s));
-    CK(launch_gen_scatter(pd, run, s));
-    CK(cudaMemsetAsync(pd.big_count, 0, sizeof(unsigned int), s));
-    CK(launch_join(pd, run, s));
-    CK(launch_join_big(pd, run, s));
-    CK(cudaMemcpyAsync(&big_h, pd.big_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    if ((double)(need[0] + need[1]) * 8.0 > (double)budget - (double)da.bytes)
+      return fail(MSP_ENOMEM, "memory budget too small for one residue class");
+    CK(ensure_rec(need));
+    int max_c = 0;
+    for (auto &pp : plan) max_c = std::max<int>(max_c, pp.c1 - pp.c0);
+    uint64_t *d_base[2];
+    uint32_t *d_cap[2], *d_fill[2];
+    unsigned int *d_ovf, *d_err;
+    for (int side = 0; side < 2; ++side) {
+      CK(da.get(&d_base[side], M));
+      CK(da.get(&d_cap[side], M));
+      CK(da.get(&d_fill[side], (size_t)max_c * nd));
+      CK(h2d(d_base[side], base_h[side].data(), sizeof(uint64_t) * M));
+      CK(h2d(d_cap[side], capv[side].data(), sizeof(uint32_t) * M));
+    }
+    CK(da.get(&d_ovf, plan.size()));
+    CK(da.get(&d_err, 1));
+    CK(cudaMemsetAsync(d_ovf, 0, sizeof(unsigned int) * plan.size(), s));
+    CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned int), s));
+    FastPass fp{};
+    fp.side[0] = gens[0];
+    fp.side[1] = gens[1];
+    fp.cmask = cmask;
+    fp.D = p.D;
+    fp.S = p.S;
+    fp.rec[0] = rec[0];
+    fp.rec[1] = rec[1];
+    fp.fill[0] = d_fill[0];
+    fp.fill[1] = d_fill[1];
+    fp.error = d_err;
+    fp.match_key = match_key;
+    fp.match_cls = match_cls;
+    fp.match_count = match_count;
+    fp.match_cap = match_cap;
+    for (size_t k = 0; k < plan.size(); ++k) {
+      if (inst->cancel && *inst->cancel) return fail(MSP_ECANCELED, "request canceled");
+      const PassPlan &pp = plan[k];
+      const int run = static_cast<int>(pp.c1 - pp.c0);
+      fp.c0 = static_cast<int>(pp.c0);
+      fp.nclass = run;
+      for (int side = 0; side < 2; ++side) {
+        fp.class_base[side] = d_base[side] + pp.c0;
+        fp.cap[side] = d_cap[side] + pp.c0;
+        CK(cudaMemsetAsync(d_fill[side], 0, sizeof(uint32_t) * (size_t)run * nd, s));
+      }
+      fp.overflow = d_ovf + k;
+      LAUNCH(MSP_K_GEN_SCATTER, 1, 8 * pp.recs, launch_scatter_fast(fp, run, s));
+      LAUNCH(MSP_K_JOIN, 1, 8 * pp.recs, launch_join_fast(fp, run, s));
+      ++passes;
+    }
+    std::vector<unsigned int> ovf_h(plan.size());
+    unsigned int err_h = 0;
+    CK(d2h(ovf_h.data(), d_ovf, sizeof(unsigned int) * plan.size()));
+    CK(d2h(&err_h, d_err, sizeof(unsigned int)));
     CK(cudaStreamSynchronize(s));
-    oversize += big_h;
-    if (big_h > pd.big_cap) return fail(MSP_EOVERFLOW, "too many oversize partitions in one pass");
-    c0 += static_cast<uint32_t>(run);
-    ++passes;
+    prof.flush();
+    if (err_h) return fail(MSP_ETIMEDOUT, "a bulk copy did not complete within its time limit");
+    for (size_t k = 0; k < plan.size(); ++k)
+      if (ovf_h[k]) exact_ranges.push_back({plan[k].c0, plan[k].c1});
+    st.fast_passes_redone = exact_ranges.size();
+  } else {
+    exact_ranges.push_back({0u, M});
+  }
+
+  if (!exact_ranges.empty()) {
+    // ---- exact passes: count, offsets, scatter, shared-memory join; any
+    //      partition larger than shared memory goes to join_big ----
+    PassDev pd{};
+    pd.cmask = cmask;
+    pd.D = p.D;
+    pd.S = p.S;
+    pd.side[0] = gens[0];
+    pd.side[1] = gens[1];
+    const double est_class[2] = {std::ldexp(1.0, p.lgL - p.B), std::ldexp(1.0, p.lgR - p.B)};
+    const size_t per_class_meta =
+        (size_t)nd * (sizeof(uint64_t) + sizeof(uint32_t)) * 2 +
+        (size_t)nd * sizeof(uint32_t) * (pd.side[0].slices + pd.side[1].slices) + 64;
+    const double per_class_bytes = (est_class[0] + est_class[1]) * 8.0 * 1.08 + per_class_meta;
+    const double room = (double)budget - (double)da.bytes + 8.0 * (double)(rec_cap[0] + rec_cap[1]);
+    if (room < fixed_reserve + per_class_bytes)
+      return fail(MSP_ENOMEM, "memory budget too small for one residue class");
+    int max_classes = static_cast<int>(std::min<double>(M, std::floor((room - fixed_reserve) / per_class_bytes)));
+    max_classes = std::max(1, std::min(max_classes, 1 << 16));
+    {
+      const uint64_t need[2] = {
+          static_cast<uint64_t>(std::min<double>(std::ldexp(1.0, p.lgL), est_class[0] * 1.08 * max_classes + 4096)),
+          static_cast<uint64_t>(std::min<double>(std::ldexp(1.0, p.lgR), est_class[1] * 1.08 * max_classes + 4096))};
+      CK(ensure_rec(need));
+    }
+    for (int side = 0; side < 2; ++side) {
+      CK(da.get(&pd.cnt[side], (size_t)max_classes * pd.side[side].slices * nd));
+      CK(da.get(&pd.segstart[side], (size_t)max_classes * nd));
+      CK(da.get(&pd.seglen[side], (size_t)max_classes * nd));
+      CK(da.get(&pd.classtot[side], (size_t)max_classes));
+      CK(da.get(&pd.classbase[side], (size_t)max_classes));
+    }
+    pd.match_key = match_key;
+    pd.match_cls = match_cls;
+    pd.match_count = match_count;
+    pd.match_cap = match_cap;
+    pd.big_cap = static_cast<uint32_t>(std::min<uint64_t>((uint64_t)max_classes * nd, 1u << 24));
+    CK(da.get(&pd.big_list, pd.big_cap));
+    CK(da.get(&pd.big_count, 1));
+
+    std::vector<uint64_t> tot_h(2 * (size_t)max_classes), base_h(2 * (size_t)max_classes);
+    unsigned int big_h = 0;
+    for (const auto &range : exact_ranges) {
+      for (uint32_t c0 = range.first; c0 < range.second;) {
+        if (inst->cancel && *inst->cancel) return fail(MSP_ECANCELED, "request canceled");
+        pd.rec[0] = rec[0];
+        pd.rec[1] = rec[1];
+        pd.c0 = static_cast<int>(c0);
+        pd.nclass = static_cast<int>(std::min<uint64_t>(max_classes, range.second - c0));
+        LAUNCH(MSP_K_GEN_COUNT, 1, 0, launch_gen_count(pd, s));
+        LAUNCH(MSP_K_OFFSETS, 1, 0, launch_counts_to_offsets(pd, s));
+        CK(d2h(tot_h.data(), pd.classtot[0], sizeof(uint64_t) * pd.nclass));
+        CK(d2h(tot_h.data() + max_classes, pd.classtot[1], sizeof(uint64_t) * pd.nclass));
+        CK(cudaStreamSynchronize(s));
+        // the longest prefix of classes that fits both record buffers
+        uint64_t acc[2] = {0, 0};
+        int run = 0;
+        for (int c = 0; c < pd.nclass; ++c) {
+          const uint64_t a0 = tot_h[c], a1 = tot_h[max_classes + c];
+          if (acc[0] + a0 > rec_cap[0] || acc[1] + a1 > rec_cap[1]) break;
+          if (a0 >= (1ull << 31) || a1 >= (1ull << 31)) break;
+          base_h[c] = acc[0];
+          base_h[max_classes + c] = acc[1];
+          acc[0] += a0;
+          acc[1] += a1;
+          ++run;
+        }
+        if (run == 0) {
+          // A class larger than the buffers (skewed class sizes): grow them
+          // to hold it if the budget allows, then retry the pass.
+          const uint64_t need[2] = {tot_h[0], tot_h[max_classes]};
+          const double need_bytes = 8.0 * (double)(need[0] + need[1]) + (double)da.bytes -
+                                    8.0 * (double)(rec_cap[0] + rec_cap[1]);
+          if (need[0] >= (1ull << 31) || need[1] >= (1ull << 31) || need_bytes > (double)budget)
+            return fail(MSP_ENOMEM, "one residue class does not fit the memory budget");
+          CK(ensure_rec(need));
+          continue;
+        }
+        CK(h2d(pd.classbase[0], base_h.data(), sizeof(uint64_t) * run));
+        CK(h2d(pd.classbase[1], base_h.data() + max_classes, sizeof(uint64_t) * run));
+        LAUNCH(MSP_K_GEN_SCATTER, 1, 8 * (acc[0] + acc[1]), launch_gen_scatter(pd, run, s));
+        CK(cudaMemsetAsync(pd.big_count, 0, sizeof(unsigned int), s));
+        LAUNCH(MSP_K_JOIN, 1, 8 * (acc[0] + acc[1]), launch_join(pd, run, s));
+        LAUNCH(MSP_K_JOIN_BIG, 1, 0, launch_join_big(pd, run, s));
+        CK(d2h(&big_h, pd.big_count, sizeof(unsigned int)));
+        CK(cudaStreamSynchronize(s));
+        prof.flush();
+        oversize += big_h;
+        if (big_h > pd.big_cap) return fail(MSP_EOVERFLOW, "too many oversize partitions in one pass");
+        c0 += static_cast<uint32_t>(run);
+        ++passes;
+      }
+    }
   }
   st.passes = passes;
   st.oversize_segments = oversize;
 
   unsigned long long nmatch = 0;
-  CK(cudaMemcpyAsync(&nmatch, pd.match_count, sizeof(nmatch), cudaMemcpyDeviceToHost, s));
+  CK(d2h(&nmatch, match_count, sizeof(nmatch)));
   CK(cudaStreamSynchronize(s));
   st.key_matches = nmatch;
-  if (nmatch > pd.match_cap) return fail(MSP_EOVERFLOW, "more than 2^20 matched keys");
+  if (nmatch > match_cap) return fail(MSP_EOVERFLOW, "more than 2^20 matched keys");
 
   if (nmatch > 0) {
     // ---- S6: recovery and exact verification ----
     RecoverDev rd{};
-    rd.match_key = pd.match_key;
-    rd.match_cls = pd.match_cls;
+    rd.match_key = match_key;
+    rd.match_cls = match_cls;
     rd.nmatch = nmatch;
-    rd.side[0] = pd.side[0];
-    rd.side[1] = pd.side[1];
+    rd.side[0] = gens[0];
+    rd.side[1] = gens[1];
     rd.oidx[0] = bd[0].idx;
     rd.iidx[0] = bd[1].idx;
     rd.oidx[1] = bd[2].idx;
@@ -429,12 +665,11 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
       CK(cudaMemsetAsync(rd.cand_count[side], 0, sizeof(unsigned long long) * nmatch, s));
       CK(cudaMemsetAsync(rd.cand_cur[side], 0, sizeof(unsigned long long) * nmatch, s));
     }
-    CK(launch_recover(rd, false, s));
+    LAUNCH(MSP_K_RECOVER, 2, 0, launch_recover(rd, false, s));
     unsigned long long ncand[2];
     for (int side = 0; side < 2; ++side) {
-      CK(launch_scan_u64(rd.cand_count[side], rd.cand_off[side], nmatch, tmp64, s));
-      CK(cudaMemcpyAsync(&ncand[side], rd.cand_off[side] + nmatch, sizeof(unsigned long long),
-                         cudaMemcpyDeviceToHost, s));
+      LAUNCH(MSP_K_RECOVER, 3, 0, launch_scan_u64(rd.cand_count[side], rd.cand_off[side], nmatch, tmp64, s));
+      CK(d2h(&ncand[side], rd.cand_off[side] + nmatch, sizeof(unsigned long long)));
     }
     CK(cudaStreamSynchronize(s));
     for (int side = 0; side < 2; ++side) {
@@ -442,7 +677,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
       CK(da.get(&rd.cand[side], ncand[side]));
     }
     CK(da.get(&rd.cand_match[0], ncand[0]));
-    CK(launch_recover(rd, true, s));
+    LAUNCH(MSP_K_RECOVER, 2, 0, launch_recover(rd, true, s));
 
     VerifyDev vd{};
     vd.ic = ic;
@@ -464,15 +699,15 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
       CK(da.get(&vd.sol, 2 * cap));
       vd.sol_cap = cap;
       CK(cudaMemsetAsync(cnts, 0, 2 * sizeof(unsigned long long), s));
-      CK(launch_verify(vd, s));
+      LAUNCH(MSP_K_VERIFY, vd.nL ? 1 : 0, 0, launch_verify(vd, s));
       unsigned long long hc[2];
-      CK(cudaMemcpyAsync(hc, cnts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+      CK(d2h(hc, cnts, sizeof(hc)));
       CK(cudaStreamSynchronize(s));
       st.pairs_verified = hc[1];
       if (hc[0] <= cap) {
         res->masks.resize(2 * hc[0]);
         if (hc[0]) {
-          CK(cudaMemcpyAsync(res->masks.data(), vd.sol, sizeof(uint64_t) * 2 * hc[0], cudaMemcpyDeviceToHost, s));
+          CK(d2h(res->masks.data(), vd.sol, sizeof(uint64_t) * 2 * hc[0]));
           CK(cudaStreamSynchronize(s));
         }
         break;
@@ -484,6 +719,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
   st.device_bytes = da.peak;
   da.release();
   CK(cudaStreamSynchronize(s));
+  prof.flush();
   return MSP_OK;
 }
 
@@ -608,6 +844,23 @@ int msp_set_stream(msp_instance *inst, void *cuda_stream) {
       return fail(MSP_ECUDA, "cudaStreamCreate failed");
     inst->own_stream = true;
   }
+  return MSP_OK;
+}
+
+int msp_set_option(msp_instance *inst, int option, int64_t value) {
+  if (!inst) return fail(MSP_EINVAL, "null instance");
+  switch (option) {
+    case MSP_OPT_EXACT_PATH:
+      inst->force_exact = value != 0;
+      return MSP_OK;
+    default:
+      return fail(MSP_EINVAL, "unknown option");
+  }
+}
+
+int msp_set_profiling(msp_instance *inst, int on) {
+  if (!inst) return fail(MSP_EINVAL, "null instance");
+  inst->profiling = on != 0;
   return MSP_OK;
 }
 

@@ -23,7 +23,7 @@ _lib = None
 
 EXPORTED_SYMBOLS = (
     "msp_create", "msp_destroy", "msp_set_stream", "msp_set_memory_budget", "msp_solve_all",
-    "msp_get_stats", "msp_free_solutions", "msp_solve_batch", "msp_server_create", "msp_submit",
+    "msp_get_stats", "msp_free_solutions", "msp_set_profiling", "msp_set_option", "msp_solve_batch", "msp_server_create", "msp_submit",
     "msp_poll", "msp_cancel", "msp_server_destroy", "msp_last_error", "msp_version",
 )
 
@@ -45,12 +45,23 @@ class Stats(ctypes.Structure):
                 ("row1_candidates_hi", ctypes.c_uint64), ("key_matches", ctypes.c_uint64),
                 ("pairs_verified", ctypes.c_uint64), ("solutions", ctypes.c_uint64),
                 ("oversize_segments", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
+                ("fast_passes_redone", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
+                ("kernel_ms", ctypes.c_double * 12), ("kernel_count", ctypes.c_uint64 * 12),
+                ("kernel_bytes", ctypes.c_uint64 * 12)]
+
+    KINDS = ("gray", "bucket", "c1", "gen_count", "offsets", "gen_scatter", "join", "join_big",
+             "recover", "verify", "other")
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["quarter"] = list(self.quarter)
         d["row1_candidates"] = int(self.row1_candidates_lo) | (int(self.row1_candidates_hi) << 64)
+        d["kernels"] = {k: {"ms": self.kernel_ms[i], "launches": int(self.kernel_count[i]),
+                            "bytes": int(self.kernel_bytes[i])}
+                        for i, k in enumerate(self.KINDS) if self.kernel_count[i]}
+        for k in ("kernel_ms", "kernel_count", "kernel_bytes"):
+            d.pop(k)
         return d
 
 
@@ -77,6 +88,8 @@ def load_library(path: str | None = None):
         lib.msp_destroy.restype = None
         lib.msp_set_stream.argtypes = [vp, vp]
         lib.msp_set_memory_budget.argtypes = [vp, ctypes.c_size_t]
+        lib.msp_set_profiling.argtypes = [vp, ctypes.c_int]
+        lib.msp_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
         lib.msp_solve_all.argtypes = [vp, ctypes.POINTER(u64p), ctypes.POINTER(ctypes.c_size_t),
                                       ctypes.POINTER(ctypes.c_int)]
         lib.msp_solve_all.restype = ctypes.c_int
@@ -120,7 +133,8 @@ def _take_masks(lib, ptr, count: int, words: int):
 class Instance:
     """One (A, d) instance: ``msp_create`` / ``msp_solve_all`` / ``msp_destroy``."""
 
-    def __init__(self, A, d, stream: int | None = None, memory_budget: int = 0):
+    def __init__(self, A, d, stream: int | None = None, memory_budget: int = 0, profiling: bool = False,
+                 exact_path: bool = False):
         lib = load_library()
         A = np.asarray(A)
         if A.ndim != 2:
@@ -138,6 +152,10 @@ class Instance:
             _check(lib.msp_set_stream(h, ctypes.c_void_p(stream)))
         if memory_budget:
             _check(lib.msp_set_memory_budget(h, ctypes.c_size_t(memory_budget)))
+        if profiling:
+            _check(lib.msp_set_profiling(h, 1))
+        if exact_path:
+            _check(lib.msp_set_option(h, 1, 1))
 
     def solve_all(self):
         ptr = ctypes.POINTER(ctypes.c_uint64)()

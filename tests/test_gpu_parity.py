@@ -241,3 +241,33 @@ def test_server_mixed_stream_matches_single_solves(msp):
                         results[i] = r
             time.sleep(0.002)
     assert [results[i] for i in ids] == alone
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_exact_path_matches_streaming_path(msp, seed):
+    # the streaming pass and the two-phase exact pass must give the same set
+    rng = np.random.default_rng(900 + seed)
+    m = int(rng.integers(2, 8))
+    n = int(rng.integers(18, 41))
+    K = int(rng.choice([3, 10, 100]))
+    A, d, _ = mi.generate(m, n, 9000 + seed, K=K, planted=True, h=n // 2)
+    want = oracle.brute(A, d) if n <= 22 else oracle.mitm(A, d)
+    with msp.Instance(A, d, exact_path=True) as inst:
+        assert inst.solve_all() == want
+    with msp.Instance(A, d) as inst:
+        assert inst.solve_all() == want
+
+
+def test_degenerate_instance_falls_back_to_exact_passes(msp):
+    # eight zero columns in Q1: every left key repeats 256 times, so the
+    # partitions of the streaming pass overflow and the exact path re-runs them
+    A, d, x = mi.generate(4, 36, 4242, planted=True, h=18)
+    A = A.copy()
+    A[:, :8] = 0
+    d = (A.astype(np.int64) @ x.astype(np.int64)).astype(np.int32)
+    with msp.Instance(A, d) as inst:
+        got = inst.solve_all()
+        st = inst.stats()
+    assert got == oracle.mitm(A, d)
+    assert len(got) >= 256
+    assert st["fast_passes_redone"] >= 1
