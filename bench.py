@@ -171,6 +171,21 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
+def traffic_per_launch(kernel, alg_bytes_per_launch):
+    """DRAM bytes per launch from the committed ncu capture, scaled by the
+    algorithmic bytes of a launch; None when the kernel source changed since."""
+    import hashlib
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        src = open(os.path.join(ROOT, t["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != t["source_sha256"]:
+            return None
+        k = t["kernels"][kernel]
+        return alg_bytes_per_launch * k["dram_bytes"] / k["algorithmic_bytes"]
+    except Exception:
+        return None
+
+
 def native(args, world, rank, local, pg):
     import torch
     from paper_2507_05045_gb300 import build
@@ -255,6 +270,8 @@ def native(args, world, rank, local, pg):
         else:
             roof = {"bound": "alu", "kernel": name, "achieved": None, "peak": None, "unit": "GB/s",
                     "frac": None, "traffic": None, "peak_source": peak_src}
+    if roof is not None and roof.get("bound") == "hbm":
+        roof["traffic"] = traffic_per_launch(roof["kernel"], roof["bytes_per_launch"])
     for k, v in byte_kernels.items():
         v["achieved_gbs"] = v["bytes"] / (v["ms"] / 1000.0) / 1e9
         v["frac_of_measured_hbm"] = v["achieved_gbs"] / hbm_peak

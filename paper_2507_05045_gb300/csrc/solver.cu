@@ -377,11 +377,22 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     g.slice_outer = std::max<int64_t>(1, (int64_t(1) << 19) / per_bucket);
     g.slices = static_cast<int>((o.size + g.slice_outer - 1) / g.slice_outer);
   }
-  // memory budget
+  // memory budget: free device memory, plus what the stream-ordered pool
+  // holds unused from earlier solves, plus this solve's own allocations
   size_t free_b = 0, total_b = 0;
   CK(cudaMemGetInfo(&free_b, &total_b));
-  size_t budget = inst->budget ? inst->budget : static_cast<size_t>(0.85 * free_b);
-  budget = std::min(budget, static_cast<size_t>(0.92 * free_b) + da.bytes);
+  {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, inst->device) == cudaSuccess) {
+      uint64_t reserved = 0, used = 0;
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+      if (reserved > used) free_b += reserved - used;
+    }
+  }
+  const double avail = (double)free_b + (double)da.bytes;
+  size_t budget = inst->budget ? inst->budget : static_cast<size_t>(0.85 * avail);
+  budget = std::min(budget, static_cast<size_t>(0.95 * avail));
   const size_t fixed_reserve = (size_t)64 << 20;  // matches and small per-pass tables
 
   uint64_t *match_key;

@@ -60,6 +60,8 @@ def main():
               [entry(6, 50, SEED_BATCH_6_50 + k, k >= 32, 25 if k >= 32 else None) for k in range(64)])
     if args.big or args.only == "7_60":
         write("sols_7_60.json", [entry(7, 60, SEED_7_60, False, None, slices=16)])
+    if args.big or args.only == "7_60_planted":
+        write("sols_7_60_planted.json", [entry(7, 60, SEED_7_60, True, 30, slices=16)])
 
 
 if __name__ == "__main__":

@@ -141,8 +141,9 @@ def test_many_passes_same_result(msp):
     assert st["passes"] >= 1
 
 
-def test_config_7_60(msp):
-    for e, A, d, x, sols in load_golden("sols_7_60.json"):
+@pytest.mark.parametrize("name", ["sols_7_60.json", "sols_7_60_planted.json"])
+def test_config_7_60(msp, name):
+    for e, A, d, x, sols in load_golden(name):
         with msp.Instance(A, d) as inst:
             got = inst.solve_all()
             st = inst.stats()
