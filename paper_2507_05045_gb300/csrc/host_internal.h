@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/msp.h"
+#include "msp_internal.cuh"
 
 struct msp_instance {
   int m = 0, n = 0;
@@ -24,6 +25,24 @@ struct msp_instance {
 };
 
 namespace msp {
+
+// Solve plan of an (m, n) instance: quarters, residue classes, digits.
+struct Plan {
+  int m, n, W;
+  int q[4], col0[4];
+  int lgL, lgR;        // log2 |L|, |R|
+  int B, t, D, S;
+  uint32_t c_row[kMaxClassRows];
+  uint64_t w_row[kMaxRows];
+};
+
+Plan make_plan(int m, int n);
+// Argument checks shared by the entry points (MSP_OK or an error status).
+int validate(const int32_t *A, const int32_t *d, int m, int n);
+// K(v) and kappa(v) of a vector of row sums under a plan.
+uint64_t key_of(const Plan &p, const int64_t *v);
+uint32_t class_of(const Plan &p, const int64_t *v);
+
 // Sets the calling thread's error text and returns `code`.
 int fail(int code, const std::string &msg);
 // msp_solve_all without the argument checks of the C entry point.

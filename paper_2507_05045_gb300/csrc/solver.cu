@@ -32,15 +32,6 @@ static uint64_t splitmix(uint64_t &s) {
   return z ^ (z >> 31);
 }
 
-struct Plan {
-  int m, n, W;
-  int q[4], col0[4];
-  int lgL, lgR;        // log2 |L|, |R|
-  int B, t, D, S;
-  uint32_t c_row[kMaxClassRows];
-  uint64_t w_row[kMaxRows];
-};
-
 // Quarters: sizes ceil(n/4) for the first n mod 4 quarters, floor(n/4) for
 // the rest; L pairs the largest quarter Q1 with Q3, R pairs Q2 with Q4.
 Plan make_plan(int m, int n) {
@@ -184,6 +175,9 @@ struct Prof {
     prof.end(kind, kernels, bytes);        \
   } while (0)
 
+}  // namespace
+
+namespace msp {
 int validate(const int32_t *A, const int32_t *d, int m, int n) {
   if (!A || !d) return fail(MSP_EINVAL, "A and d must be non-null");
   if (m < 1 || m > kMaxRows) return fail(MSP_ERANGE, "m must lie in [1, 16]");
@@ -211,6 +205,9 @@ uint32_t class_of(const Plan &p, const int64_t *v) {
   for (int i = 0; i < p.t; ++i) c += p.c_row[i] * static_cast<uint32_t>(v[i]);
   return p.B ? (c & ((1u << p.B) - 1u)) : 0u;
 }
+}  // namespace msp
+
+namespace {
 
 struct SolveResult {
   std::vector<uint64_t> masks;  // [count][2]
