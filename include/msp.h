@@ -161,6 +161,29 @@ MSP_API int msp_poll(msp_server *srv, uint64_t req_id, uint64_t **masks, size_t 
 MSP_API int msp_cancel(msp_server *srv, uint64_t req_id);
 MSP_API void msp_server_destroy(msp_server *srv);
 
+/* Exhaustive solve of a small instance (n <= 40) that allocates no device
+ * memory.  The paper has no counterpart: it is for callers that cannot
+ * allocate device memory while solving - a process whose device memory is
+ * owned (and possibly fully reserved) by another framework's allocator, a
+ * serving loop that must not risk an out-of-memory failure or an allocator
+ * stall mid-request, or code running under a fixed device-memory quota.
+ * It runs the same kernels as msp_solve_all (the exact two-phase residue
+ * pass) with every intermediate buffer taken from one static device array of
+ * 24 MiB that each device holding the library keeps until process exit.
+ *   A (m x n row-major) and d (m): host inputs, copied during the call.
+ *   masks: caller-owned host buffer of `cap` uint64 (one word per solution,
+ *   since n <= 40); on MSP_OK it holds *count sorted distinct solutions.
+ *   stream: cudaStream_t (as void*) to run on; NULL = the legacy stream.
+ *   Errors: MSP_ERANGE for n > 40 (and the usual limits), MSP_EOVERFLOW when
+ *   the solutions exceed `cap` (then *count is an upper bound to retry with)
+ *   or the static scratch (more than 8192 matched keys, 131072 candidates or
+ *   131072 solutions).
+ * The first call on a device resolves the array's address (with that device
+ * current) and should come before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU race: serialise them. */
+MSP_API int msp_solve_small_noalloc(const int32_t *A, const int32_t *d, int m, int n, uint64_t *masks,
+                                    size_t cap, size_t *count, void *stream);
+
 /* Thread-local description of the last error (never NULL). */
 MSP_API const char *msp_last_error(void);
 

@@ -25,6 +25,7 @@ EXPORTED_SYMBOLS = (
     "msp_create", "msp_destroy", "msp_set_stream", "msp_set_memory_budget", "msp_solve_all",
     "msp_get_stats", "msp_free_solutions", "msp_set_profiling", "msp_set_option", "msp_solve_batch", "msp_server_create", "msp_submit",
     "msp_poll", "msp_cancel", "msp_server_destroy", "msp_last_error", "msp_version",
+    "msp_solve_small_noalloc",
 )
 
 STATUS = {0: "MSP_OK", 1: "MSP_PENDING", -1: "MSP_EINVAL", -2: "MSP_ERANGE", -3: "MSP_ENOMEM",
@@ -105,6 +106,9 @@ def load_library(path: str | None = None):
         lib.msp_cancel.argtypes = [vp, ctypes.c_uint64]
         lib.msp_server_destroy.argtypes = [vp]
         lib.msp_server_destroy.restype = None
+        lib.msp_solve_small_noalloc.argtypes = [i32p, i32p, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_size_t,
+                                                ctypes.POINTER(ctypes.c_size_t), vp]
+        lib.msp_solve_small_noalloc.restype = ctypes.c_int
         lib.msp_last_error.restype = ctypes.c_char_p
         lib.msp_version.restype = ctypes.c_char_p
         _lib = lib
@@ -267,3 +271,18 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def solve_small_noalloc(A, d, cap: int = 1 << 16, stream: int | None = None):
+    """``msp_solve_small_noalloc``: the solve of a small instance (n <= 40)
+    without device allocation; same result as :func:`solve_all`."""
+    lib = load_library()
+    A = np.asarray(A)
+    m, n = A.shape
+    a, ap = _i32(A)
+    dd, dp = _i32(np.asarray(d).reshape(-1))
+    out = np.zeros(max(1, cap), dtype=np.uint64)
+    cnt = ctypes.c_size_t()
+    _check(lib.msp_solve_small_noalloc(ap, dp, m, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), cap,
+                                       ctypes.byref(cnt), ctypes.c_void_p(stream) if stream else None))
+    return [(int(v),) for v in out[:cnt.value]]
