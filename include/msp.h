@@ -85,6 +85,9 @@ typedef struct {
   uint64_t fast_passes_redone;/* streaming passes re-run on the exact path    */
   uint64_t h2d_bytes;         /* host-to-device bytes copied by the solve     */
   uint64_t d2h_bytes;         /* device-to-host bytes copied by the solve     */
+  uint64_t classes_total;     /* residue classes of the instance (2^class_bits) */
+  uint64_t classes_done;      /* classes this solve enumerated                */
+  uint64_t records_done;      /* half-pair records (both sides) it generated   */
   /* Filled only when profiling is on (msp_set_profiling): per kernel kind
    * (MSP_K_* below) the summed CUDA-event time, the launches, and the
    * algorithmic device-memory bytes (records written / read x 8 bytes). */
@@ -127,7 +130,14 @@ MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
  *                       pass on the exact two-phase path (count, then
  *                       scatter); 0 = default (streaming, exact re-run of
  *                       any pass whose partitions overflow). */
-enum { MSP_OPT_EXACT_PATH = 1 };
+/*   MSP_OPT_CLASS_PART, MSP_OPT_CLASS_PARTS  enumerate only the residue
+ *                       classes [k*M/P, (k+1)*M/P) of the M classes, with
+ *                       k = PART and P = PARTS (default 0 of 1: all).  The
+ *                       solutions of the P parts are disjoint and their union
+ *                       is the full solution set, so parts can be solved by
+ *                       different processes or GPUs, or one part timed to
+ *                       project the full time (records_done / all records). */
+enum { MSP_OPT_EXACT_PATH = 1, MSP_OPT_CLASS_PART = 2, MSP_OPT_CLASS_PARTS = 3 };
 MSP_API int msp_set_option(msp_instance *inst, int option, int64_t value);
 
 /* Time every kernel launch of later solves with CUDA events (on = 1). */

@@ -22,6 +22,7 @@ struct msp_instance {
   int device = 0;
   bool profiling = false;
   bool force_exact = false;
+  int64_t part = 0, parts = 1;  // residue-class subset [part*M/parts, (part+1)*M/parts)
 };
 
 namespace msp {
@@ -31,7 +32,7 @@ struct Plan {
   int m, n, W;
   int q[4], col0[4];
   int lgL, lgR;        // log2 |L|, |R|
-  int B, t, D, S;
+  int B, t, D, Dx, S;  // D: streaming-pass digits, Dx: exact-pass digits
   uint32_t c_row[kMaxClassRows];
   uint64_t w_row[kMaxRows];
 };

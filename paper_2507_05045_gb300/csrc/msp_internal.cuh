@@ -76,6 +76,7 @@ struct SideGen {
   const uint32_t *ioff;
   int64_t slice_outer;  // outer elements per slice
   int slices;           // slices per class
+  int wmax;             // outer elements per window of the streaming scatter
 };
 
 struct PassDev {
@@ -103,7 +104,7 @@ struct PassDev {
 };
 
 // Streaming pass (fastpath.cu): partitions of fixed capacity <= kFastCap.
-constexpr int kFastCap = 4864;
+constexpr int kFastCap = 8960;
 
 struct FastPass {
   SideGen side[2];

@@ -144,7 +144,7 @@ extern "C" int msp_solve_small_noalloc(const int32_t *A, const int32_t *d, int m
   ic.kd = key_of(p, dv);
   ic.cd = class_of(p, dv);
   const uint32_t M = 1u, cmask = 0u;
-  const int nd = 1 << p.D;
+  const int nd = 1 << p.Dx;
 
   // ---- carve every buffer out of the static scratch ----
   Carve cv{scratch};
@@ -174,7 +174,7 @@ extern "C" int msp_solve_small_noalloc(const int32_t *A, const int32_t *d, int m
   uint32_t *d_scantmp = cv.take<uint32_t>(4);
   PassDev pd{};
   pd.cmask = cmask;
-  pd.D = p.D;
+  pd.D = p.Dx;
   pd.S = p.S;
   for (int side = 0; side < 2; ++side) {
     const BucketDev &o = bd[side == 0 ? 0 : 2];

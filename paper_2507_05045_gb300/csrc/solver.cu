@@ -51,10 +51,16 @@ Plan make_plan(int m, int n) {
   // about 2^22 records per class and side, partitions of about 2^12
   // (1024 digits); the exact class-size convolution needs 2^B <= 2^18.
   p.B = std::min(18, std::max(0, lgmax - 22));
-  p.t = p.B <= 8 ? 1 : (p.B <= 14 ? 2 : 3);
+  // row 1 alone while its residues stay uniform (2^B <= 256 against a
+  // row-1 spread of a few hundred); three rows beyond, which keeps the class
+  // sizes within about one percent of each other
+  p.t = p.B <= 8 ? 1 : 3;
   p.t = std::min(p.t, m);
-  p.D = std::min(12, std::max(0, lgmax - p.B - 12));
-  p.S = 10;  // 1024 shared-memory buckets per side (about 4 keys each)
+  // streaming pass: partitions of about 2^13 records (512 digits for a
+  // class of 2^22); exact two-phase pass: about 2^12 (1024 digits)
+  p.D = std::min(12, std::max(0, lgmax - p.B - 13));
+  p.Dx = std::min(12, std::max(0, lgmax - p.B - 12));
+  p.S = 11;  // 2048 shared-memory buckets per partition side
   uint64_t s = 0x2507050450000001ull;
   p.c_row[0] = 1;
   for (int i = 1; i < kMaxClassRows; ++i) p.c_row[i] = static_cast<uint32_t>(splitmix(s)) | 1u;
@@ -373,6 +379,8 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     const int64_t per_bucket = std::max<int64_t>(1, in.size / M);
     g.slice_outer = std::max<int64_t>(1, (int64_t(1) << 19) / per_bucket);
     g.slices = static_cast<int>((o.size + g.slice_outer - 1) / g.slice_outer);
+    // a window should cover about two rounds of 4096 records
+    g.wmax = static_cast<int>(std::min<int64_t>(1024, std::max<int64_t>(32, 8192 / per_bucket)));
   }
   // memory budget: free device memory, plus what the stream-ordered pool
   // holds unused from earlier solves, plus this solve's own allocations
@@ -417,6 +425,11 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     return cudaSuccess;
   };
 
+  if (inst->part >= inst->parts) return fail(MSP_EINVAL, "class part must be below the number of parts");
+  const uint32_t c_begin = static_cast<uint32_t>((uint64_t)M * inst->part / inst->parts);
+  const uint32_t c_end = static_cast<uint32_t>((uint64_t)M * (inst->part + 1) / inst->parts);
+  st.classes_total = M;
+  st.classes_done = c_end - c_begin;
   int passes = 0;
   uint64_t oversize = 0;
   std::vector<std::pair<uint32_t, uint32_t>> exact_ranges;
@@ -436,16 +449,14 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     }
     CK(cudaStreamSynchronize(s));
     prof.flush();
-    for (int side = 0; side < 2 && fast; ++side)
+    // partition capacity mean + 6.5 sigma + 16, a multiple of 16 records; a
+    // class whose partitions would exceed kFastCap takes the exact path
+    for (int side = 0; side < 2; ++side)
       for (uint32_t c = 0; c < M; ++c) {
         const double mean = (double)csz[side][c] / nd;
-        uint64_t cap = static_cast<uint64_t>(std::ceil(mean + 8.0 * std::sqrt(mean) + 32.0));
+        uint64_t cap = static_cast<uint64_t>(std::ceil(mean + 6.5 * std::sqrt(mean) + 16.0));
         cap = (cap + 15) & ~uint64_t(15);
-        if (cap > (uint64_t)kFastCap) {
-          fast = false;
-          break;
-        }
-        capv[side][c] = static_cast<uint32_t>(cap);
+        capv[side][c] = cap > (uint64_t)kFastCap ? 0u : static_cast<uint32_t>(cap);
       }
   }
   if (fast) {
@@ -466,10 +477,19 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     std::vector<PassPlan> plan;
     std::vector<uint64_t> base_h[2] = {std::vector<uint64_t>(M), std::vector<uint64_t>(M)};
     uint64_t need[2] = {0, 0};
-    for (uint32_t c0 = 0; c0 < M;) {
+    for (uint32_t c = c_begin; c < c_end; ++c) st.records_done += csz[0][c] + csz[1][c];
+    for (uint32_t c0 = c_begin; c0 < c_end;) {
+      if (capv[0][c0] == 0 || capv[1][c0] == 0) {  // oversized class: exact path
+        if (!exact_ranges.empty() && exact_ranges.back().second == c0)
+          exact_ranges.back().second = c0 + 1;
+        else
+          exact_ranges.push_back({c0, c0 + 1});
+        ++c0;
+        continue;
+      }
       uint64_t acc[2] = {0, 0}, recs = 0;
       uint32_t c = c0;
-      while (c < M && (int)(c - c0) < max_run) {
+      while (c < c_end && (int)(c - c0) < max_run && capv[0][c] && capv[1][c]) {
         const uint64_t r0 = (uint64_t)capv[0][c] * nd, r1 = (uint64_t)capv[1][c] * nd;
         if (c > c0 && (acc[0] + r0 > lim[0] || acc[1] + r1 > lim[1])) break;
         base_h[0][c] = acc[0];
@@ -542,18 +562,21 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     prof.flush();
     if (err_h) return fail(MSP_ETIMEDOUT, "a bulk copy did not complete within its time limit");
     for (size_t k = 0; k < plan.size(); ++k)
-      if (ovf_h[k]) exact_ranges.push_back({plan[k].c0, plan[k].c1});
-    st.fast_passes_redone = exact_ranges.size();
-  } else {
-    exact_ranges.push_back({0u, M});
+      if (ovf_h[k]) {
+        exact_ranges.push_back({plan[k].c0, plan[k].c1});
+        ++st.fast_passes_redone;
+      }
+  } else if (c_begin < c_end) {
+    exact_ranges.push_back({c_begin, c_end});
   }
 
   if (!exact_ranges.empty()) {
+    const int nd = 1 << p.Dx;  // exact pass digits
     // ---- exact passes: count, offsets, scatter, shared-memory join; any
     //      partition larger than shared memory goes to join_big ----
     PassDev pd{};
     pd.cmask = cmask;
-    pd.D = p.D;
+    pd.D = p.Dx;
     pd.S = p.S;
     pd.side[0] = gens[0];
     pd.side[1] = gens[1];
@@ -615,6 +638,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
           acc[1] += a1;
           ++run;
         }
+        if (!fast) st.records_done += acc[0] + acc[1];
         if (run == 0) {
           // A class larger than the buffers (skewed class sizes): grow them
           // to hold it if the budget allows, then retry the pass.
@@ -860,6 +884,14 @@ int msp_set_option(msp_instance *inst, int option, int64_t value) {
   switch (option) {
     case MSP_OPT_EXACT_PATH:
       inst->force_exact = value != 0;
+      return MSP_OK;
+    case MSP_OPT_CLASS_PART:
+      if (value < 0) return fail(MSP_EINVAL, "class part must be >= 0");
+      inst->part = value;
+      return MSP_OK;
+    case MSP_OPT_CLASS_PARTS:
+      if (value < 1) return fail(MSP_EINVAL, "class parts must be >= 1");
+      inst->parts = value;
       return MSP_OK;
     default:
       return fail(MSP_EINVAL, "unknown option");

@@ -48,6 +48,8 @@ class Stats(ctypes.Structure):
                 ("oversize_segments", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("ms_total", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
                 ("fast_passes_redone", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
+                ("classes_total", ctypes.c_uint64), ("classes_done", ctypes.c_uint64),
+                ("records_done", ctypes.c_uint64),
                 ("kernel_ms", ctypes.c_double * 12), ("kernel_count", ctypes.c_uint64 * 12),
                 ("kernel_bytes", ctypes.c_uint64 * 12)]
 
@@ -138,7 +140,7 @@ class Instance:
     """One (A, d) instance: ``msp_create`` / ``msp_solve_all`` / ``msp_destroy``."""
 
     def __init__(self, A, d, stream: int | None = None, memory_budget: int = 0, profiling: bool = False,
-                 exact_path: bool = False):
+                 exact_path: bool = False, class_part: tuple[int, int] | None = None):
         lib = load_library()
         A = np.asarray(A)
         if A.ndim != 2:
@@ -160,6 +162,9 @@ class Instance:
             _check(lib.msp_set_profiling(h, 1))
         if exact_path:
             _check(lib.msp_set_option(h, 1, 1))
+        if class_part is not None:
+            _check(lib.msp_set_option(h, 3, int(class_part[1])))
+            _check(lib.msp_set_option(h, 2, int(class_part[0])))
 
     def solve_all(self):
         ptr = ctypes.POINTER(ctypes.c_uint64)()

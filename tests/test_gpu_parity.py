@@ -272,3 +272,24 @@ def test_degenerate_instance_falls_back_to_exact_passes(msp):
     assert got == oracle.mitm(A, d)
     assert len(got) >= 256
     assert st["fast_passes_redone"] >= 1
+
+
+def test_class_parts_partition_the_solution_set(msp):
+    # the solutions of the residue-class parts are disjoint and their union
+    # is the full set; records_done adds up to all records
+    A, d, x = mi.generate(6, 50, 4321, K=20, planted=True, h=25)
+    with msp.Instance(A, d) as inst:
+        full = inst.solve_all()
+        st_full = inst.stats()
+    parts, union, recs = 4, [], 0
+    for k in range(parts):
+        with msp.Instance(A, d, class_part=(k, parts)) as inst:
+            got = inst.solve_all()
+            st = inst.stats()
+        assert set(got).isdisjoint(union)
+        union += got
+        recs += st["records_done"]
+        assert st["classes_done"] * parts == st["classes_total"]
+    assert sorted(union) == full
+    assert recs == st_full["records_done"] == st_full["records_left"] + st_full["records_right"]
+    assert mi.mask_of(x) in full
