@@ -170,10 +170,12 @@ constexpr int kCsU = 1024;
 
 __global__ void __launch_bounds__(kCsR) class_size_kernel(const uint32_t *__restrict__ offO,
                                                           const uint32_t *__restrict__ offI, uint32_t M,
+                                                          uint32_t rbeg, uint32_t rcount,
                                                           unsigned long long *out) {
   __shared__ uint32_t sO[kCsU];
   __shared__ uint32_t sI[kCsU + kCsR];
-  const uint32_t r0 = blockIdx.x * kCsR;
+  const uint32_t r0 = rbeg + blockIdx.x * kCsR;  // classes of this block: [r0, r0 + kCsR)
+  const uint32_t ri = blockIdx.x * kCsR + threadIdx.x;
   const uint32_t r = r0 + threadIdx.x;
   const uint32_t mask = M - 1u;
   unsigned long long acc = 0;
@@ -188,23 +190,24 @@ __global__ void __launch_bounds__(kCsR) class_size_kernel(const uint32_t *__rest
       sI[k] = offI[w + 1] - offI[w];
     }
     __syncthreads();
-    if (r < M) {
+    if (ri < rcount) {
       // u = u0 + i  ->  k = (r - r0) + (nu - 1) - i
       const uint32_t kb = threadIdx.x + (nu - 1);
       for (uint32_t i = 0; i < nu; ++i) acc += static_cast<unsigned long long>(sO[i]) * sI[kb - i];
     }
     __syncthreads();
   }
-  if (r < M) out[r] = acc;
+  if (ri < rcount) out[ri] = acc;
+  (void)r;
 }
 
-cudaError_t launch_class_sizes(const uint32_t *offO, const uint32_t *offI, uint32_t M, unsigned long long *out,
-                               cudaStream_t s) {
-  const uint32_t blocks = (M + kCsR - 1) / kCsR;
-  class_size_kernel<<<blocks, kCsR, 0, s>>>(offO, offI, M, out);
+cudaError_t launch_class_sizes(const uint32_t *offO, const uint32_t *offI, uint32_t M, uint32_t rbeg,
+                               uint32_t rcount, unsigned long long *out, cudaStream_t s) {
+  if (rcount == 0) return cudaSuccess;
+  const uint32_t blocks = (rcount + kCsR - 1) / kCsR;
+  class_size_kernel<<<blocks, kCsR, 0, s>>>(offO, offI, M, rbeg, rcount, out);
   return cudaGetLastError();
 }
-
 
 // -------------------------------------------------------------------------
 // Scatter (S3 + the first radix digit of S4).
@@ -269,35 +272,38 @@ __global__ void __launch_bounds__(kScT, 3) scatter_fast_kernel(FastPass p, int n
   const int warp = threadIdx.x >> 5;
   for (int wu = blockIdx.x; wu < nwu; wu += gridDim.x) {
     int side, cl, sl;
+    const int per_inst = p.nclass * (p.slices[0] + p.slices[1]);
+    const int inst_i = wu / per_inst;
+    const FastInst &fi = p.inst[inst_i];
     {
-      const int nb0 = p.nclass * p.side[0].slices;
-      int b = wu;
+      const int nb0 = p.nclass * p.slices[0];
+      int b = wu % per_inst;
       if (b < nb0) {
         side = 0;
       } else {
         side = 1;
         b -= nb0;
       }
-      cl = b / p.side[side].slices;
-      sl = b % p.side[side].slices;
+      cl = b / p.slices[side];
+      sl = b % p.slices[side];
     }
-    // the side's lists in registers (a runtime index into the parameter
-    // struct would copy it to local memory)
-    const uint64_t *__restrict__ okey = side ? p.side[1].okey : p.side[0].okey;
-    const uint32_t *__restrict__ ocls = side ? p.side[1].ocls : p.side[0].ocls;
-    const uint64_t *__restrict__ ikey = side ? p.side[1].ikey : p.side[0].ikey;
-    const uint32_t *__restrict__ ioff = side ? p.side[1].ioff : p.side[0].ioff;
-    const int64_t osize = side ? p.side[1].osize : p.side[0].osize;
-    const int64_t slice_outer = side ? p.side[1].slice_outer : p.side[0].slice_outer;
-    const int wmax = side ? p.side[1].wmax : p.side[0].wmax;
-    const uint32_t r = static_cast<uint32_t>(p.c0 + cl) & p.cmask;
+    const SideGen &g = fi.side[side];
+    const uint64_t *__restrict__ okey = g.okey;
+    const uint32_t *__restrict__ ocls = g.ocls;
+    const uint64_t *__restrict__ ikey = g.ikey;
+    const uint32_t *__restrict__ ioff = g.ioff;
+    const int64_t osize = g.osize;
+    const int64_t slice_outer = g.slice_outer;
+    const int wmax = g.wmax;
+    const uint32_t cg_id = static_cast<uint32_t>(p.c0 + cl);
+    const uint32_t r = cg_id & p.cmask;
     const int64_t o_end = min((int64_t)(sl + 1) * slice_outer, osize);
     int64_t o_cur = (int64_t)sl * slice_outer;
     uint32_t j_cur = 0;
-    const uint32_t cap = p.cap[side][cl];
-    const unsigned long long seg0 = p.class_base[side][cl];
+    const uint32_t cap = fi.cap[side][cg_id];
+    const unsigned long long seg0 = fi.class_base[side][cg_id];
     uint64_t *const rec = p.rec[side];
-    uint32_t *const fill = p.fill[side] + (int64_t)cl * nd;
+    uint32_t *const fill = fi.fill[side] + (int64_t)cl * nd;
 
     while (o_cur < o_end) {
       // ---- 1. window ----
@@ -422,7 +428,7 @@ __global__ void __launch_bounds__(kScT, 3) scatter_fast_kernel(FastPass p, int n
           desc[gd] = dd;
         }
       }
-      if (ovf) atomicOr(p.overflow, 1u);
+      if (ovf) atomicOr(p.overflow + inst_i, 1u);
       // ---- 4. place by digit, then write the runs ----
       if (K0 < n_round) {
 #pragma unroll
@@ -465,7 +471,7 @@ static cudaError_t launch_scatter_d(const FastPass &p, int nclass_run, cudaStrea
   }
   FastPass q = p;
   q.nclass = nclass_run;
-  const int nwu = nclass_run * (p.side[0].slices + p.side[1].slices);
+  const int nwu = p.ninst * nclass_run * (p.slices[0] + p.slices[1]);
   const int blocks = std::max(1, std::min(nwu, per_sm * sms));
   scatter_fast_kernel<D><<<blocks, kScT, smem, s>>>(q, nwu);
   return cudaGetLastError();
@@ -511,18 +517,24 @@ size_t join_fast_smem(int S) {
 struct SegRef {
   const uint64_t *L, *R;
   uint32_t nL, nR;
+  uint32_t cls;  // tag + class id of the partition
 };
 
 __device__ __forceinline__ SegRef seg_ref(const FastPass &p, int s) {
   const int nd = 1 << p.D;
-  const int cl = s >> p.D, gd = s & (nd - 1);
+  const int per_inst = p.nclass << p.D;
+  const FastInst &fi = p.inst[s / per_inst];
+  const int rem = s % per_inst;
+  const int cl = rem >> p.D, gd = rem & (nd - 1);
+  const uint32_t cg_id = static_cast<uint32_t>(p.c0 + cl);
   SegRef r;
-  const uint32_t capL = p.cap[0][cl], capR = p.cap[1][cl];
-  r.L = p.rec[0] + p.class_base[0][cl] + (uint64_t)gd * capL;
-  r.R = p.rec[1] + p.class_base[1][cl] + (uint64_t)gd * capR;
-  r.nL = min(p.fill[0][(int64_t)cl * nd + gd], capL);
-  r.nR = min(p.fill[1][(int64_t)cl * nd + gd], capR);
+  const uint32_t capL = fi.cap[0][cg_id], capR = fi.cap[1][cg_id];
+  r.L = p.rec[0] + fi.class_base[0][cg_id] + (uint64_t)gd * capL;
+  r.R = p.rec[1] + fi.class_base[1][cg_id] + (uint64_t)gd * capR;
+  r.nL = min(fi.fill[0][(int64_t)cl * nd + gd], capL);
+  r.nR = min(fi.fill[1][(int64_t)cl * nd + gd], capR);
   if (r.nL == 0 || r.nR == 0) r.nL = r.nR = 0;
+  r.cls = fi.tag + (cg_id & p.cmask);
   return r;
 }
 
@@ -651,7 +663,7 @@ __global__ void __launch_bounds__(kJT, 1) join_fast_kernel(FastPass p, int nseg)
     if (!wait_phase(&barR, phR, p.error, &s_ok)) return;  // includes a block barrier
     phR ^= 1u;
     if (r.nR) {
-      const uint32_t cls = static_cast<uint32_t>(p.c0 + (s >> D)) & p.cmask;
+      const uint32_t cls = r.cls;
       const uint32_t rounds = (r.nR + kJT - 1) / kJT;
       for (uint32_t rd = 0; rd < rounds; ++rd) {
         const uint32_t i = rd * kJT + threadIdx.x;
@@ -695,10 +707,12 @@ static cudaError_t launch_join_d(const FastPass &p, int nclass_run, cudaStream_t
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  const int nseg = nclass_run << D;
+  FastPass q = p;
+  q.nclass = nclass_run;
+  const int nseg = p.ninst * (nclass_run << D);
   const int blocks = std::min(nseg, sms);
   if (blocks < 1) return cudaSuccess;
-  join_fast_kernel<D><<<blocks, kJT, smem, s>>>(p, nseg);
+  join_fast_kernel<D><<<blocks, kJT, smem, s>>>(q, nseg);
   return cudaGetLastError();
 }
 

@@ -48,6 +48,10 @@ uint32_t class_of(const Plan &p, const int64_t *v);
 int fail(int code, const std::string &msg);
 // msp_solve_all without the argument checks of the C entry point.
 int solve_instance(msp_instance *inst, uint64_t **masks, size_t *count, int *words);
+// Solve count instances of one (m, n) together on stream s (raw[k]: unsorted
+// two-word masks of instance k); budget 0 = most of the free device memory.
+int solve_batch_impl(const int32_t *const *A, const int32_t *const *d, int m, int n, int count,
+                     std::vector<std::vector<uint64_t>> &raw, cudaStream_t s, size_t budget);
 // Device bytes of the quarter lists plus one residue pass (capped at cap).
 size_t footprint_estimate(int m, int n, size_t cap);
 }  // namespace msp

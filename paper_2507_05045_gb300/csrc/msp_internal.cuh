@@ -106,24 +106,34 @@ struct PassDev {
 // Streaming pass (fastpath.cu): partitions of fixed capacity <= kFastCap.
 constexpr int kFastCap = 8960;
 
-struct FastPass {
+// One instance of a streaming pass (device table; a single solve has one
+// entry, a batch one per instance of the same (m, n)).
+struct FastInst {
   SideGen side[2];
+  const uint64_t *class_base[2];  // [M] first record of each class region (by class id)
+  const uint32_t *cap[2];         // [M] records per partition (multiple of 16)
+  uint32_t *fill[2];              // [nclass of the pass][2^D] records appended (zeroed per pass)
+  uint32_t tag;                   // added to the class id of emitted matches (instance * M)
+};
+
+struct FastPass {
+  const FastInst *inst;           // [ninst] in device memory
+  int ninst;
+  int slices[2];                  // slices per class and side (same for every instance)
   uint32_t cmask;
-  int c0, nclass;
+  int c0, nclass;                 // classes [c0, c0 + nclass) of every instance
   int D, S;
-  const uint64_t *class_base[2];  // [nclass] first record of the class region
-  const uint32_t *cap[2];         // [nclass] records per partition (multiple of 16)
-  uint32_t *fill[2];              // [nclass][2^D] records appended (zeroed per pass)
   uint64_t *rec[2];
-  unsigned int *overflow;         // this pass dropped a record (partition full)
+  unsigned int *overflow;         // [ninst]: the instance dropped a record (partition full)
   unsigned int *error;            // a bounded wait gave up
   uint64_t *match_key;
-  uint32_t *match_cls;
+  uint32_t *match_cls;            // tag + class
   unsigned long long *match_count;
   uint64_t match_cap;
 };
-cudaError_t launch_class_sizes(const uint32_t *offO, const uint32_t *offI, uint32_t M, unsigned long long *out,
-                               cudaStream_t s);
+// out[i] = exact size of class rbeg + i, i < rcount (classes mod M).
+cudaError_t launch_class_sizes(const uint32_t *offO, const uint32_t *offI, uint32_t M, uint32_t rbeg,
+                               uint32_t rcount, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_scatter_fast(const FastPass &p, int nclass_run, cudaStream_t s);
 cudaError_t launch_join_fast(const FastPass &p, int nclass_run, cudaStream_t s);
 size_t scatter_fast_smem(int D);

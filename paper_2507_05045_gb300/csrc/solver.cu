@@ -4,6 +4,7 @@
 #include "msp_internal.cuh"
 #include "../../include/msp.h"
 #include "host_internal.h"
+#include "host_util.h"
 
 #include <algorithm>
 #include <chrono>
@@ -50,11 +51,12 @@ Plan make_plan(int m, int n) {
   const int lgmax = std::max(p.lgL, p.lgR);
   // about 2^22 records per class and side, partitions of about 2^12
   // (1024 digits); the exact class-size convolution needs 2^B <= 2^18.
-  p.B = std::min(18, std::max(0, lgmax - 22));
+  p.B = std::min(23, std::max(0, lgmax - 22));
   // row 1 alone while its residues stay uniform (2^B <= 256 against a
   // row-1 spread of a few hundred); three rows beyond, which keeps the class
-  // sizes within about one percent of each other
-  p.t = p.B <= 8 ? 1 : 3;
+  // sizes within about one percent of each other (four rows past 2^18
+  // classes)
+  p.t = p.B <= 8 ? 1 : (p.B <= 18 ? 3 : 4);
   p.t = std::min(p.t, m);
   // streaming pass: partitions of about 2^13 records (512 digits for a
   // class of 2^22); exact two-phase pass: about 2^12 (1024 digits)
@@ -73,113 +75,6 @@ Plan make_plan(int m, int n) {
 using namespace msp;
 
 namespace {
-
-struct DevAlloc {
-  cudaStream_t s;
-  std::vector<void *> ptrs;
-  size_t bytes = 0, peak = 0;
-  explicit DevAlloc(cudaStream_t st) : s(st) {}
-  template <typename T>
-  cudaError_t get(T **p, size_t count) {
-    void *q = nullptr;
-    const size_t b = std::max<size_t>(count, 1) * sizeof(T);
-    cudaError_t e = cudaMallocAsync(&q, b, s);
-    if (e != cudaSuccess) return e;
-    ptrs.push_back(q);
-    bytes += b;
-    peak = std::max(peak, bytes);
-    *p = static_cast<T *>(q);
-    return cudaSuccess;
-  }
-  void free1(void *q, size_t b) {
-    for (auto &x : ptrs)
-      if (x == q) {
-        cudaFreeAsync(q, s);
-        x = nullptr;
-        bytes -= b;
-        return;
-      }
-  }
-  void release() {
-    for (void *q : ptrs)
-      if (q) cudaFreeAsync(q, s);
-    ptrs.clear();
-    bytes = 0;
-  }
-  ~DevAlloc() { release(); }
-};
-
-#define CK(call)                                                                      \
-  do {                                                                                \
-    cudaError_t e_ = (call);                                                          \
-    if (e_ != cudaSuccess) {                                                          \
-      return fail(e_ == cudaErrorMemoryAllocation ? MSP_ENOMEM : MSP_ECUDA,           \
-                  std::string(#call) + ": " + cudaGetErrorString(e_));                \
-    }                                                                                 \
-  } while (0)
-
-// Per-launch CUDA-event timing (only when the instance has profiling on)
-// and launch counting (always).
-struct Prof {
-  bool on = false;
-  cudaStream_t s = nullptr;
-  msp_stats *st = nullptr;
-  struct Item {
-    int kind;
-    cudaEvent_t a, b;
-  };
-  std::vector<Item> pending;
-  std::vector<cudaEvent_t> pool;
-  cudaEvent_t get() {
-    if (!pool.empty()) {
-      cudaEvent_t e = pool.back();
-      pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
-  }
-  cudaEvent_t a_ = nullptr;
-  void begin() {
-    if (!on) return;
-    a_ = get();
-    cudaEventRecord(a_, s);
-  }
-  void end(int kind, int kernels, uint64_t bytes) {
-    st->kernel_launches += kernels;
-    if (!on) return;
-    cudaEvent_t b = get();
-    cudaEventRecord(b, s);
-    pending.push_back({kind, a_, b});
-    st->kernel_count[kind] += kernels;
-    st->kernel_bytes[kind] += bytes;
-  }
-  // call after the stream reached the recorded events
-  void flush() {
-    for (auto &it : pending) {
-      float ms = 0;
-      if (cudaEventElapsedTime(&ms, it.a, it.b) == cudaSuccess) st->kernel_ms[it.kind] += ms;
-      pool.push_back(it.a);
-      pool.push_back(it.b);
-    }
-    pending.clear();
-  }
-  ~Prof() {
-    for (auto &it : pending) {
-      cudaEventDestroy(it.a);
-      cudaEventDestroy(it.b);
-    }
-    for (auto e : pool) cudaEventDestroy(e);
-  }
-};
-
-#define LAUNCH(kind, kernels, bytes, call) \
-  do {                                     \
-    prof.begin();                          \
-    CK(call);                              \
-    prof.end(kind, kernels, bytes);        \
-  } while (0)
 
 }  // namespace
 
@@ -433,30 +328,35 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
   int passes = 0;
   uint64_t oversize = 0;
   std::vector<std::pair<uint32_t, uint32_t>> exact_ranges;
-  bool fast = !inst->force_exact && M <= (1u << 18);
+  bool fast = !inst->force_exact && c_begin < c_end;
   std::vector<unsigned long long> csz[2];
   std::vector<uint32_t> capv[2];
   if (fast) {
-    // exact class sizes by convolution of the bucket histograms (S2)
+    // exact sizes of the classes to enumerate, by convolution of the bucket
+    // histograms (S2); O(M) work per class
+    const uint32_t ncl = c_end - c_begin;
     unsigned long long *d_csz;
-    CK(da.get(&d_csz, 2 * (size_t)M));
-    LAUNCH(MSP_K_OTHER, 1, 0, launch_class_sizes(bd[0].off, bd[1].off, M, d_csz, s));
-    LAUNCH(MSP_K_OTHER, 1, 0, launch_class_sizes(bd[2].off, bd[3].off, M, d_csz + M, s));
+    CK(da.get(&d_csz, 2 * (size_t)ncl));
+    LAUNCH(MSP_K_OTHER, 1, 0, launch_class_sizes(bd[0].off, bd[1].off, M, c_begin, ncl, d_csz, s));
+    LAUNCH(MSP_K_OTHER, 1, 0, launch_class_sizes(bd[2].off, bd[3].off, M, c_begin, ncl, d_csz + ncl, s));
     for (int side = 0; side < 2; ++side) {
-      csz[side].resize(M);
-      capv[side].resize(M);
-      CK(d2h(csz[side].data(), d_csz + (size_t)side * M, sizeof(unsigned long long) * M));
+      csz[side].assign(M, 0);
+      capv[side].assign(M, 0);
+      CK(d2h(csz[side].data() + c_begin, d_csz + (size_t)side * ncl, sizeof(unsigned long long) * ncl));
     }
     CK(cudaStreamSynchronize(s));
     prof.flush();
-    // partition capacity mean + 6.5 sigma + 16, a multiple of 16 records; a
-    // class whose partitions would exceed kFastCap takes the exact path
+    da.free1(d_csz, sizeof(unsigned long long) * 2 * ncl);
+    // partition capacity mean + 7 sigma + 32 (a multiple of 16 records,
+    // at most kFastCap); a class whose partitions would not hold even
+    // mean + 4 sigma takes the exact path
     for (int side = 0; side < 2; ++side)
-      for (uint32_t c = 0; c < M; ++c) {
+      for (uint32_t c = c_begin; c < c_end; ++c) {
         const double mean = (double)csz[side][c] / nd;
-        uint64_t cap = static_cast<uint64_t>(std::ceil(mean + 6.5 * std::sqrt(mean) + 16.0));
-        cap = (cap + 15) & ~uint64_t(15);
-        capv[side][c] = cap > (uint64_t)kFastCap ? 0u : static_cast<uint32_t>(cap);
+        uint64_t cap = static_cast<uint64_t>(std::ceil(mean + 7.0 * std::sqrt(mean) + 32.0));
+        cap = std::min<uint64_t>((cap + 15) & ~uint64_t(15), kFastCap);
+        const bool fits = mean + 4.0 * std::sqrt(mean) <= (double)kFastCap;
+        capv[side][c] = fits ? static_cast<uint32_t>(cap) : 0u;
       }
   }
   if (fast) {
@@ -465,7 +365,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     const double rec_budget = std::max(0.0, (double)budget - (double)da.bytes - (double)fixed_reserve);
     double tot_region[2] = {0, 0};
     for (int side = 0; side < 2; ++side)
-      for (uint32_t c = 0; c < M; ++c) tot_region[side] += (double)capv[side][c] * nd;
+      for (uint32_t c = c_begin; c < c_end; ++c) tot_region[side] += (double)capv[side][c] * nd;
     const double frac0 = tot_region[0] / std::max(1.0, tot_region[0] + tot_region[1]);
     const uint64_t lim[2] = {static_cast<uint64_t>(rec_budget / 8.0 * frac0),
                              static_cast<uint64_t>(rec_budget / 8.0 * (1.0 - frac0))};
@@ -523,16 +423,27 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     CK(da.get(&d_err, 1));
     CK(cudaMemsetAsync(d_ovf, 0, sizeof(unsigned int) * plan.size(), s));
     CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned int), s));
+    FastInst fi{};
+    for (int side = 0; side < 2; ++side) {
+      fi.side[side] = gens[side];
+      fi.class_base[side] = d_base[side];
+      fi.cap[side] = d_cap[side];
+      fi.fill[side] = d_fill[side];
+    }
+    fi.tag = 0;
+    FastInst *d_fi;
+    CK(da.get(&d_fi, 1));
+    CK(h2d(d_fi, &fi, sizeof(FastInst)));
     FastPass fp{};
-    fp.side[0] = gens[0];
-    fp.side[1] = gens[1];
+    fp.inst = d_fi;
+    fp.ninst = 1;
+    fp.slices[0] = gens[0].slices;
+    fp.slices[1] = gens[1].slices;
     fp.cmask = cmask;
     fp.D = p.D;
     fp.S = p.S;
     fp.rec[0] = rec[0];
     fp.rec[1] = rec[1];
-    fp.fill[0] = d_fill[0];
-    fp.fill[1] = d_fill[1];
     fp.error = d_err;
     fp.match_key = match_key;
     fp.match_cls = match_cls;
@@ -544,11 +455,8 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
       const int run = static_cast<int>(pp.c1 - pp.c0);
       fp.c0 = static_cast<int>(pp.c0);
       fp.nclass = run;
-      for (int side = 0; side < 2; ++side) {
-        fp.class_base[side] = d_base[side] + pp.c0;
-        fp.cap[side] = d_cap[side] + pp.c0;
+      for (int side = 0; side < 2; ++side)
         CK(cudaMemsetAsync(d_fill[side], 0, sizeof(uint32_t) * (size_t)run * nd, s));
-      }
       fp.overflow = d_ovf + k;
       LAUNCH(MSP_K_GEN_SCATTER, 1, 8 * pp.recs, launch_scatter_fast(fp, run, s));
       LAUNCH(MSP_K_JOIN, 1, 8 * pp.recs, launch_join_fast(fp, run, s));
@@ -926,21 +834,37 @@ int msp_solve_batch(const int32_t *const *A, const int32_t *const *d, int m, int
                     uint64_t **masks, size_t *offsets) {
   if (!A || !d || !masks || !offsets || count < 0) return fail(MSP_EINVAL, "null argument");
   *masks = nullptr;
-  const int W = (n + 63) / 64;
-  std::vector<uint64_t> all;
   offsets[0] = 0;
   for (int k = 0; k < count; ++k) {
-    msp_instance *inst = nullptr;
-    int rc = msp_create(A[k], d[k], m, n, &inst);
+    const int rc = validate(A[k], d[k], m, n);
     if (rc != MSP_OK) return rc;
-    uint64_t *mk = nullptr;
-    size_t c = 0;
-    rc = msp_solve_all(inst, &mk, &c, nullptr);
-    msp_destroy(inst);
-    if (rc != MSP_OK) return rc;
-    all.insert(all.end(), mk, mk + c * W);
-    msp_free_solutions(mk);
-    offsets[k + 1] = offsets[k] + c;
+  }
+  if (count == 0) return MSP_OK;
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1)
+    return fail(MSP_ECUDA, "no CUDA device available");
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(MSP_ECUDA, "cudaStreamCreate failed");
+  std::vector<std::vector<uint64_t>> raw;
+  const int rc = msp::solve_batch_impl(A, d, m, n, count, raw, s, 0);
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (rc != MSP_OK) return rc;
+  // sort and de-duplicate each instance's masks (most significant word first)
+  const int W = (n + 63) / 64;
+  std::vector<uint64_t> all;
+  for (int k = 0; k < count; ++k) {
+    const size_t cnt = raw[k].size() / 2;
+    std::vector<std::pair<uint64_t, uint64_t>> v(cnt);
+    for (size_t i = 0; i < cnt; ++i) v[i] = {raw[k][2 * i + 1], raw[k][2 * i]};
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    for (auto &x : v) {
+      all.push_back(x.second);
+      if (W > 1) all.push_back(x.first);
+    }
+    offsets[k + 1] = offsets[k] + v.size();
   }
   if (!all.empty()) {
     *masks = static_cast<uint64_t *>(std::malloc(sizeof(uint64_t) * all.size()));
