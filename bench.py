@@ -52,6 +52,13 @@ def parse():
     ap.add_argument("--m", type=int, default=M_)
     ap.add_argument("--n", type=int, default=N_)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", choices=["9_80", "batch_6_50", "serving", "10_90_part"], default="9_80",
+                    help="9_80 (default): the headline exhaustive solve; batch_6_50: 64 (6,50) "
+                         "instances in one batched call vs one at a time; serving: the mixed Poisson "
+                         "request stream through the server vs sequential solving; 10_90_part: one "
+                         "seeded 1/64 of the residue classes of a (10,90) instance")
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--rate-factor", type=float, default=0.8)
     return ap.parse_args()
 
 
@@ -333,12 +340,197 @@ def reference(args, world, rank, pg):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Secondary workloads (rank 0, one GPU): batched, served, (10,90) part.
+# ---------------------------------------------------------------------------
+def _emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def bench_batch(args):
+    import paper_2507_05045_gb300 as msp
+    from paper_2507_05045_gb300 import build
+    build.build()
+    insts = mi.batch(6, 50, 64, 1000, h=25)
+    pairs = [(A, d) for A, d, _ in insts]
+    for _ in range(args.warmup):
+        msp.solve_batch(pairs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rb = msp.solve_batch(pairs)
+    tb = (time.perf_counter() - t0) / args.steps
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rs = [msp.solve_all(A, d) for A, d in pairs]
+    ts = (time.perf_counter() - t0) / args.steps
+    assert rb == rs
+    h2d = sum(A.nbytes + d.nbytes for A, d in pairs)
+    d2h = sum(len(r) * 8 for r in rb)
+    _emit({"metric": "instances/s, 64 (6,50) instances per batched call", "value": 64 / tb,
+           "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u64", "data": "synthetic",
+           "config": {"workload": "64 (6,50) instances, seeds 1000..1063, 32 plain + 32 planted (25 ones)",
+                      "l2": "pass buffers of ~37 GB, larger than L2"},
+           "sequential": {"value": 64 / ts, "unit": "instances/s", "ms_per_step": ts * 1e3},
+           "speedup_vs_sequential": ts / tb,
+           "e2e": {"value": 64 / tb, "unit": "instances/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h}})
+
+
+SERVE_SHAPES = [(4, 30), (5, 40), (6, 50), (7, 60), (8, 70)]
+
+
+def serving_trace(nreq, seed=4242):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(nreq):
+        m, n = SERVE_SHAPES[int(rng.integers(0, len(SERVE_SHAPES)))]
+        planted = bool(rng.integers(0, 2))
+        A, d, _ = mi.generate(m, n, 50000 + k, planted=planted, h=n // 2)
+        reqs.append((A, d))
+    gaps = rng.exponential(1.0, size=nreq)  # scaled by 1/lambda later
+    return reqs, gaps
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q / 100.0 * (len(xs) - 1))))]
+
+
+def bench_serving(args):
+    import threading
+    import paper_2507_05045_gb300 as msp
+    from paper_2507_05045_gb300 import build
+    build.build()
+    reqs, gaps = serving_trace(args.requests)
+    # sequential service rate of the mix, measured on one solve per shape
+    svc = []
+    for (m, n) in SERVE_SHAPES:
+        A, d, _ = mi.generate(m, n, 7)
+        msp.solve_all(A, d)
+        t0 = time.perf_counter()
+        msp.solve_all(A, d)
+        svc.append(time.perf_counter() - t0)
+    mean_svc = float(np.mean(svc))
+    lam = args.rate_factor / mean_svc
+    arrivals = np.cumsum(gaps / lam)
+
+    def run_sequential():
+        lat, t_start = [], time.perf_counter()
+        clock = 0.0
+        results = []
+        for (A, d), at in zip(reqs, arrivals):
+            now = time.perf_counter() - t_start
+            if now < at:
+                time.sleep(at - now)
+            results.append(msp.solve_all(A, d))
+            lat.append(time.perf_counter() - t_start - at)
+        return lat, time.perf_counter() - t_start, results
+
+    def run_served():
+        srv = msp.Server(max_inflight=4)
+        ids = [None] * len(reqs)
+        done_at = [None] * len(reqs)
+        results = [None] * len(reqs)
+        t_start = time.perf_counter()
+        sub_done = threading.Event()
+
+        def submitter():
+            for k, ((A, d), at) in enumerate(zip(reqs, arrivals)):
+                now = time.perf_counter() - t_start
+                if now < at:
+                    time.sleep(at - now)
+                ids[k] = srv.submit(A, d)
+            sub_done.set()
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        pending = set()
+        nxt = 0
+        while True:
+            while nxt < len(reqs) and ids[nxt] is not None:
+                pending.add(nxt)
+                nxt += 1
+            for k in list(pending):
+                r = srv.poll(ids[k])
+                if r is not None:
+                    results[k] = r
+                    done_at[k] = time.perf_counter() - t_start
+                    pending.discard(k)
+            if sub_done.is_set() and nxt == len(reqs) and not pending:
+                break
+            time.sleep(0.0005)
+        th.join()
+        srv.close()
+        lat = [done_at[k] - arrivals[k] for k in range(len(reqs))]
+        return lat, time.perf_counter() - t_start, results
+
+    lat_s, span_s, res_s = run_served()
+    lat_q, span_q, res_q = run_sequential()
+    same = res_s == res_q
+    out = {"metric": "p50/p99 latency, mixed stream (time from arrival to all solutions)",
+           "value": len(reqs) / span_s, "unit": "requests/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+           "ms_per_step": span_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u64", "data": "synthetic",
+           "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {args.rate_factor} x the "
+                                  f"sequential service rate ({lam:.2f}/s), (m,n) uniform over "
+                                  f"{SERVE_SHAPES}, 50% planted", "max_inflight": 4},
+           "served": {"p50_ms": _pct(lat_s, 50) * 1e3, "p99_ms": _pct(lat_s, 99) * 1e3,
+                      "throughput_rps": len(reqs) / span_s},
+           "sequential": {"p50_ms": _pct(lat_q, 50) * 1e3, "p99_ms": _pct(lat_q, 99) * 1e3,
+                          "throughput_rps": len(reqs) / span_q},
+           "results_identical": same, "mean_service_s": mean_svc,
+           "e2e": {"value": len(reqs) / span_s, "unit": "requests/s",
+                   "h2d_bytes_per_step": int(sum(A.nbytes + d.nbytes for A, d in reqs)),
+                   "d2h_bytes_per_step": int(sum(len(r) * 8 for r in res_s))}}
+    _emit(out)
+
+
+def bench_10_90(args):
+    import paper_2507_05045_gb300 as msp
+    from paper_2507_05045_gb300 import build
+    build.build()
+    part = (37, 64)  # fixed, seeded choice of one 1/64 of the residue classes
+    A, d, _ = mi.generate(10, 90, 1090)
+    with msp.Instance(A, d, class_part=part, profiling=True) as inst:
+        for _ in range(args.warmup):
+            inst.solve_all()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            inst.solve_all()
+        dt = (time.perf_counter() - t0) / args.steps
+        st = inst.stats()
+    total = st["records_left"] + st["records_right"]
+    proj = dt * total / st["records_done"]
+    c1 = st["row1_candidates"]
+    _emit({"metric": "candidate pairs/s at (10,90) over a seeded 1/64 of the residue classes "
+                     "(projected full time)", "value": c1 / proj, "unit": "candidate pairs/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+           "data": "synthetic",
+           "config": {"workload": "(10,90) plain instance seed 1090, classes part 37 of 64",
+                      "l2": "pass buffers of tens of GB, larger than L2"},
+           "projected_full_time_s": proj, "records_done": st["records_done"], "records_total": total,
+           "classes_done": st["classes_done"], "classes_total": st["classes_total"],
+           "kernels": st["kernels"]})
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_init(args)
     try:
         if args.impl == "reference":
             reference(args, world, rank, pg)
+        elif args.config == "batch_6_50":
+            if rank == 0:
+                bench_batch(args)
+        elif args.config == "serving":
+            if rank == 0:
+                bench_serving(args)
+        elif args.config == "10_90_part":
+            if rank == 0:
+                bench_10_90(args)
         else:
             native(args, world, rank, local, pg)
     finally:

@@ -715,12 +715,16 @@ int solve_instance(msp_instance *inst, uint64_t **masks, size_t *count, int *wor
 size_t footprint_estimate(int m, int n, size_t cap) {
   const Plan p = make_plan(m, n);
   double fixed = 0;
+  // quarter lists (packed rows, key, class, row 1) and their class buckets
   for (int k = 0; k < 4; ++k) fixed += std::ldexp(1.0, p.q[k]) * (8.0 * p.W + 16.0 + 16.0);
-  fixed += 4.0 * std::ldexp(1.0, p.B) * 4.0 + (64 << 20);
-  const double cls = (std::ldexp(1.0, p.lgL - p.B) + std::ldexp(1.0, p.lgR - p.B)) * 8.0 * 1.08;
+  // per-class tables (bucket offsets, class sizes, partition bases and caps)
+  fixed += 64.0 * std::ldexp(1.0, p.B);
+  // matched keys, the exact path's reserve, and a margin
+  fixed += (12 << 20) + (64 << 20) + (64 << 20);
+  const double cls = (std::ldexp(1.0, p.lgL - p.B) + std::ldexp(1.0, p.lgR - p.B)) * 8.0 * 1.1;
   const double all = cls * std::ldexp(1.0, p.B);
-  double want = fixed + std::min(all, std::max(cls, 4.0 * (1 << 30)));
-  if (cap && want > (double)cap) want = std::max<double>(cap, fixed + cls);
+  double want = fixed + std::min(all, std::max(2.0 * cls, 4.0 * (1 << 30)));
+  if (cap && want > (double)cap) want = std::max<double>(cap, fixed + 2.0 * cls);
   return static_cast<size_t>(want);
 }
 
