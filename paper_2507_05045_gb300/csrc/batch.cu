@@ -238,7 +238,7 @@ int solve_batch_impl(const int32_t *const *A, const int32_t *const *d, int m, in
       const int64_t per_bucket = std::max<int64_t>(1, in.size / M);
       g.slice_outer = std::max<int64_t>(1, (int64_t(1) << 19) / per_bucket);
       g.slices = static_cast<int>((o.size + g.slice_outer - 1) / g.slice_outer);
-      g.wmax = static_cast<int>(std::min<int64_t>(1024, std::max<int64_t>(32, 8192 / per_bucket)));
+      g.wmax = scatter_window(in.size, M);
       CK(launch_class_sizes(side == 0 ? it.bd[0].off : it.bd[2].off, side == 0 ? it.bd[1].off : it.bd[3].off, M, 0,
                             M, d_csz + ((size_t)t * 2 + side) * M, s));
     }

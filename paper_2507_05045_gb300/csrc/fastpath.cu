@@ -1,20 +1,16 @@
 // Streaming pass of libmsp (sm_103a): the records of a residue pass are
-// generated once, radix-partitioned through a thread-block cluster, and
-// joined by a persistent kernel fed with bulk asynchronous copies.
+// generated once, radix-partitioned by the top D key bits into partitions of
+// fixed capacity, and joined by a persistent kernel fed with bulk
+// asynchronous copies.
 //
 //   class_size_kernel   exact class sizes |L_r| = sum_u |Q1[u]| |Q3[r-u]|
 //                       (cyclic convolution of the bucket histograms).
-//   scatter_fast_kernel per cluster round every block generates up to 8192
-//                       records into registers and ranks them by the top D
-//                       key bits in shared memory; the blocks of the cluster
-//                       exchange their digit histograms through distributed
-//                       shared memory, one owner block per digit reserves
-//                       the cluster's run with a single global atomic, and
-//                       every block writes its part of the run, so a digit's
-//                       records leave the cluster as one contiguous run.
-//                       Partitions have a fixed capacity (mean + 8 sigma);
-//                       a record past it raises the pass's overflow flag and
-//                       the host re-runs that pass on the exact path.
+//   scatter_fast_kernel per round a block generates 4096 records into
+//                       registers, ranks them by digit in shared memory,
+//                       reserves each digit's run with one global atomic and
+//                       writes the runs contiguously.  A record past its
+//                       partition's capacity raises the instance's overflow
+//                       flag and the host re-runs that pass on the exact path.
 //   join_fast_kernel    persistent: while a partition is sorted and joined
 //                       in shared memory, the next one is already streaming
 //                       in by cp.async.bulk (1-D TMA) on an mbarrier.
@@ -213,27 +209,32 @@ cudaError_t launch_class_sizes(const uint32_t *offO, const uint32_t *offI, uint3
 // Scatter (S3 + the first radix digit of S4).
 // A block owns a slice of one class (side, class, outer range) and walks it
 // in rounds of up to kScRound records.  Each round:
-//   1. window: up to kScW outer elements, their inner buckets r - kappa(o),
-//      and a block scan of the bucket sizes; empty buckets are compacted out,
-//      so the record prefix over the window is strictly increasing;
-//   2. generation: warp w takes records [w*512, w*512 + 512) in 16 batches
-//      of 32 consecutive records.  The lane of record K + lane finds its
-//      outer element without branching: the starts of the next 32 elements
-//      that fall inside the batch are OR-reduced into a 32-bit mask and the
-//      element is e0 + popcount(mask & lanes<=lane).  key = K(o) + K(i);
-//   3. rank by the top D key bits (shared atomics), block scan of the digit
-//      histogram, one global atomic per nonempty digit reserves this round's
-//      run in the partition (class, digit);
-//   4. records are placed by digit in shared memory and leave as contiguous
-//      runs (one write burst per digit).
+//   1. window: up to wmax outer elements, their inner buckets r - kappa(o)
+//      and a block scan of the bucket sizes.  Nonempty elements are
+//      compacted: element e keeps its outer key and delta(e) = (first inner
+//      index) - (first record of e in the round), so record k of the round
+//      reads inner index delta(e) + k; a bitmap marks the record at which
+//      each element starts;
+//   2. generation: warp w owns records [256 w, 256 w + 256).  The element of
+//      record k is (elements starting before the warp's range) + popcount of
+//      the bitmap bits up to k, minus one; key = K(o) + K(i), ranked by its
+//      top D bits with a shared-memory atomic; keys and ranks stay in
+//      registers;
+//   3. digit offsets by a block scan, one global atomic per nonempty digit
+//      reserves the round's run in the partition (class, digit);
+//   4. keys are placed by digit in shared memory (over the window arrays,
+//      which are dead by then) and leave as contiguous runs.
 // Partitions have a fixed capacity; a record past it is dropped and the
-// pass's overflow flag raised (the host re-runs that pass on the exact path).
+// instance's overflow flag raised (the host re-runs that pass on the exact
+// path).
 // -------------------------------------------------------------------------
-constexpr int kScT = 256;                    // threads per block
-constexpr int kScBatches = 16;               // batches of 32 records per warp and round
-constexpr int kScRound = kScT * kScBatches;  // 4096 records per round
-constexpr int kScE = 4;                      // outer elements per thread in a window
-constexpr int kScW = kScT * kScE;            // 1024 outer elements per window
+constexpr int kScT = 512;                   // threads per block
+constexpr int kScPer = 8;                   // records per thread and round
+constexpr int kScRound = kScT * kScPer;     // 4096 records per round
+constexpr int kScE = 4;                     // outer elements per thread in a window
+constexpr int kScW = kScT * kScE;           // at most 2048 outer elements per window
+constexpr int kScWords = kScRound / 32;     // bitmap words
+static_assert(kScW <= kScRound, "compacted elements must fit the window arrays");
 
 struct __align__(16) DigitDesc {
   unsigned long long dst;  // record index of sorted position 0 of this digit's run
@@ -241,207 +242,277 @@ struct __align__(16) DigitDesc {
   uint32_t pad;
 };
 
+int scatter_window(int64_t inner_size, uint32_t classes) {
+  // outer elements whose inner buckets hold about one round of records
+  const double avg = std::max(1.0 / 64, (double)inner_size / (double)std::max<uint32_t>(1, classes));
+  const double w = (double)kScRound / avg;
+  return static_cast<int>(std::min<double>(kScW, std::max<double>(32, w)));
+}
+
 size_t scatter_fast_smem(int D) {
   const size_t nd = size_t(1) << D;
-  return kScRound * sizeof(uint64_t)         // records placed by digit
-         + kScW * sizeof(uint64_t)           // outer keys of the window
-         + nd * sizeof(DigitDesc)            // per-digit destinations
-         + kScW * sizeof(uint32_t)           // inner bucket starts
-         + (kScW + 1) * sizeof(uint32_t)     // record prefix of the window
-         + 2 * nd * sizeof(uint32_t)         // histogram, local offsets
-         + kScW * sizeof(uint16_t)           // window index of each nonempty element
+  return (size_t)kScRound * (sizeof(uint64_t) + sizeof(uint32_t))  // outer keys + deltas / sorted keys
+         + nd * sizeof(DigitDesc)                                   // per-digit destinations
+         + 2 * nd * sizeof(uint32_t)                                // histogram, local offsets
+         + kScWords * sizeof(uint32_t)                              // element-start bitmap
          + 64;
 }
 
+// Block-uniform state of the work unit being scattered.  It lives in shared
+// memory and every phase re-reads what it needs after the block barrier, so
+// the keys and ranks of a round, not loop invariants, hold the registers.
+struct ScatterUnit {
+  const uint64_t *okey;
+  const uint32_t *ocls;
+  const uint64_t *ikey;
+  const uint32_t *ioff;
+  uint64_t *rec;
+  uint32_t *fill;
+  unsigned long long seg0;
+  long long o_cur, o_end;
+  uint32_t j_cur, cap, r, wmax;
+  int inst;
+};
+
 template <int D>
-__global__ void __launch_bounds__(kScT, 3) scatter_fast_kernel(FastPass p, int nwu) {
+__global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPass p, int nwu) {
   extern __shared__ __align__(16) uint8_t sm[];
   constexpr int nd = 1 << D;
-  uint64_t *sorted = reinterpret_cast<uint64_t *>(sm);
-  uint64_t *s_ko = sorted + kScRound;
-  DigitDesc *desc = reinterpret_cast<DigitDesc *>(s_ko + kScW);
-  uint32_t *s_ib = reinterpret_cast<uint32_t *>(desc + nd);
-  uint32_t *s_pre = s_ib + kScW;
-  uint32_t *hist = s_pre + kScW + 1;
-  uint32_t *loff = hist + nd;
-  uint16_t *s_orig = reinterpret_cast<uint16_t *>(loff + nd);
+  constexpr int pd = nd > kScT ? nd / kScT : 1;  // digits per thread in the digit phase
+  uint64_t *const s_ko = reinterpret_cast<uint64_t *>(sm);            // window: outer key of element e
+  uint64_t *const sorted = s_ko;                                      // placement: keys by digit
+  uint32_t *const s_delta = reinterpret_cast<uint32_t *>(s_ko + kScRound);
+  DigitDesc *const desc = reinterpret_cast<DigitDesc *>(s_delta + kScRound);
+  uint32_t *const hist = reinterpret_cast<uint32_t *>(desc + nd);
+  uint32_t *const loff = hist + nd;
+  uint32_t *const bm = loff + nd;
   __shared__ unsigned long long s_wt64[32];
   __shared__ uint32_t s_wt[32];
+  __shared__ ScatterUnit u;
+  __shared__ long long s_next_o;
+  __shared__ uint32_t s_next_j;
 
   const int lanei = static_cast<int>(lane());
-  const int warp = threadIdx.x >> 5;
+  const uint32_t lemask = (2u << lanei) - 1u;  // lanes <= this lane
+  for (int i = threadIdx.x; i < nd; i += kScT) hist[i] = 0;
+
   for (int wu = blockIdx.x; wu < nwu; wu += gridDim.x) {
-    int side, cl, sl;
-    const int per_inst = p.nclass * (p.slices[0] + p.slices[1]);
-    const int inst_i = wu / per_inst;
-    const FastInst &fi = p.inst[inst_i];
-    {
+    __syncthreads();  // the previous unit's last round has read u
+    if (threadIdx.x == 0) {
+      const int per_inst = p.nclass * (p.slices[0] + p.slices[1]);
+      const int inst_i = wu / per_inst;
+      const FastInst &fi = p.inst[inst_i];
       const int nb0 = p.nclass * p.slices[0];
       int b = wu % per_inst;
-      if (b < nb0) {
-        side = 0;
-      } else {
+      int side = 0;
+      if (b >= nb0) {
         side = 1;
         b -= nb0;
       }
-      cl = b / p.slices[side];
-      sl = b % p.slices[side];
+      const int ns = side ? p.slices[1] : p.slices[0];
+      const int cl = b / ns, sl = b % ns;
+      const SideGen &g = fi.side[side];
+      const uint32_t cg_id = static_cast<uint32_t>(p.c0 + cl);
+      u.okey = g.okey;
+      u.ocls = g.ocls;
+      u.ikey = g.ikey;
+      u.ioff = g.ioff;
+      u.rec = side ? p.rec[1] : p.rec[0];
+      u.fill = fi.fill[side] + (int64_t)cl * nd;
+      u.seg0 = fi.class_base[side][cg_id];
+      u.o_cur = (int64_t)sl * g.slice_outer;
+      u.o_end = min((int64_t)(sl + 1) * g.slice_outer, g.osize);
+      u.j_cur = 0;
+      u.cap = fi.cap[side][cg_id];
+      u.r = cg_id & p.cmask;
+      u.wmax = static_cast<uint32_t>(g.wmax);
+      u.inst = inst_i;
     }
-    const SideGen &g = fi.side[side];
-    const uint64_t *__restrict__ okey = g.okey;
-    const uint32_t *__restrict__ ocls = g.ocls;
-    const uint64_t *__restrict__ ikey = g.ikey;
-    const uint32_t *__restrict__ ioff = g.ioff;
-    const int64_t osize = g.osize;
-    const int64_t slice_outer = g.slice_outer;
-    const int wmax = g.wmax;
-    const uint32_t cg_id = static_cast<uint32_t>(p.c0 + cl);
-    const uint32_t r = cg_id & p.cmask;
-    const int64_t o_end = min((int64_t)(sl + 1) * slice_outer, osize);
-    int64_t o_cur = (int64_t)sl * slice_outer;
-    uint32_t j_cur = 0;
-    const uint32_t cap = fi.cap[side][cg_id];
-    const unsigned long long seg0 = fi.class_base[side][cg_id];
-    uint64_t *const rec = p.rec[side];
-    uint32_t *const fill = fi.fill[side] + (int64_t)cl * nd;
+    __syncthreads();
 
-    while (o_cur < o_end) {
-      // ---- 1. window ----
-      const int w_n = static_cast<int>(min(static_cast<int64_t>(wmax), o_end - o_cur));
+    while (u.o_cur < u.o_end) {
+      // ---- 1. window: element idx = e * kScT + thread (coalesced) ----
+      const long long o_cur = u.o_cur;
+      const uint32_t j_cur = u.j_cur;
+      const int w_n = static_cast<int>(min(static_cast<long long>(u.wmax), u.o_end - o_cur));
       uint32_t cnt[kScE], ibv[kScE];
       uint64_t kov[kScE];
-      unsigned long long recs = 0;
-      uint32_t nonempty = 0;
-#pragma unroll
-      for (int e = 0; e < kScE; ++e) {
-        const int idx = threadIdx.x * kScE + e;
-        cnt[e] = 0;
-        if (idx < w_n) {
-          const int64_t o = o_cur + idx;
-          const uint32_t w = (r - ocls[o]) & p.cmask;
-          uint32_t ib = ioff[w];
-          uint32_t c = ioff[w + 1] - ib;
-          if (idx == 0) {
-            ib += j_cur;
-            c -= j_cur;
-          }
-          cnt[e] = c;
-          ibv[e] = ib;
-          kov[e] = okey[o];
-          recs += c;
-          nonempty += c ? 1u : 0u;
-        }
-      }
-      for (int i = threadIdx.x; i < nd; i += kScT) hist[i] = 0;
-      unsigned long long tot_packed;
-      // low 12 bits: nonempty elements (< 4096), high bits: records
-      const unsigned long long ex =
-          scan_excl<unsigned long long>((recs << 12) | nonempty, s_wt64, &tot_packed);
       {
-        uint32_t pos = static_cast<uint32_t>(ex & 0xfffu);
-        unsigned long long pre = ex >> 12;
+        const uint32_t *__restrict__ ocls = u.ocls;
+        const uint32_t *__restrict__ ioff = u.ioff;
+        const uint64_t *__restrict__ okey = u.okey;
+        const uint32_t r = u.r, cmask = p.cmask;
 #pragma unroll
         for (int e = 0; e < kScE; ++e) {
-          if (cnt[e]) {
-            s_ko[pos] = kov[e];
-            s_ib[pos] = ibv[e];
-            s_pre[pos] = static_cast<uint32_t>(min(pre, 0xffffffffull));
-            s_orig[pos] = static_cast<uint16_t>(threadIdx.x * kScE + e);
-            ++pos;
-            pre += cnt[e];
-          }
-        }
-      }
-      const uint32_t nne = static_cast<uint32_t>(tot_packed & 0xfffu);
-      const unsigned long long total = tot_packed >> 12;
-      if (threadIdx.x == 0) s_pre[nne] = static_cast<uint32_t>(min(total, 0xffffffffull));
-      __syncthreads();
-      const uint32_t n_round = static_cast<uint32_t>(min(static_cast<unsigned long long>(kScRound), total));
-
-      // ---- 2. generation: 16 batches of 32 consecutive records per warp ----
-      uint64_t keys[kScBatches];
-      uint32_t rank[kScBatches];
-      const uint32_t K0 = static_cast<uint32_t>(warp) * (kScBatches * 32);
-      if (K0 < n_round) {
-        uint32_t lo = 0, hi = nne - 1;  // last element whose prefix is <= K0
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi + 1) >> 1;
-          if (s_pre[mid] <= K0) lo = mid; else hi = mid - 1;
-        }
-        uint32_t e0 = lo;             // element holding record K of the batch
-        uint32_t st0 = s_pre[lo];     // its first record
-        const uint32_t lemask = (2u << lanei) - 1u;  // lanes <= this lane
-#pragma unroll
-        for (int b = 0; b < kScBatches; ++b) {
-          const uint32_t K = K0 + b * 32;
-          if (K < n_round) {  // warp-uniform
-            const uint32_t t = e0 + 1 + lanei;
-            const uint32_t P = t <= nne ? s_pre[t] : 0xffffffffu;
-            const uint32_t off = P - K;  // >= 1: element e0 holds record K
-            const unsigned mask = __reduce_or_sync(0xffffffffu, off < 32u ? (1u << off) : 0u);
-            const uint32_t c = __popc(mask & lemask);
-            const uint32_t shp = __shfl_sync(0xffffffffu, P, (c - 1u) & 31u);
-            const uint32_t e = e0 + c;
-            const uint32_t start = c ? shp : st0;
-            const uint32_t k = K + lanei;
-            if (k < n_round) {
-              const uint64_t key = s_ko[e] + ikey[s_ib[e] + (k - start)];
-              keys[b] = key;
-              rank[b] = atomicAdd(&hist[digit_t<D>(key)], 1u);
+          const int idx = e * kScT + threadIdx.x;
+          cnt[e] = 0;
+          ibv[e] = 0;
+          kov[e] = 0;
+          // clamped so that the addresses stay inside the slice for every lane
+          const long long o = o_cur + min(idx, w_n - 1);
+          if (idx < w_n) {
+            kov[e] = okey[o];
+            const uint32_t w = (r - ocls[o]) & cmask;
+            uint32_t ib = ioff[w];
+            uint32_t c = ioff[w + 1] - ib;
+            if (idx == 0) {
+              ib += j_cur;
+              c -= j_cur;
             }
-            e0 = __shfl_sync(0xffffffffu, e, 31);
-            st0 = __shfl_sync(0xffffffffu, start, 31);
+            cnt[e] = c;
+            ibv[e] = ib;
           }
         }
       }
-      __syncthreads();
-      // ---- advance the cursor past this round's records ----
-      if (n_round == total) {
-        o_cur += w_n;
-        j_cur = 0;
-      } else {
-        uint32_t lo = 0, hi = nne - 1;
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi + 1) >> 1;
-          if (s_pre[mid] <= n_round) lo = mid; else hi = mid - 1;
-        }
-        const uint32_t oi = s_orig[lo];
-        j_cur = (n_round - s_pre[lo]) + (oi == 0 ? j_cur : 0u);
-        o_cur += oi;
+      for (int i = threadIdx.x; i < kScWords; i += kScT) bm[i] = 0;
+      if (threadIdx.x == 0) {
+        s_next_o = o_cur + w_n;
+        s_next_j = 0;
       }
+      // Element slices in order; a scan per slice (records in the high bits,
+      // nonempty elements in the low 13) gives each element its first record
+      // and its compacted position.
+      unsigned long long rec_carry = 0;
+      uint32_t pos_carry = 0;
+#pragma unroll
+      for (int e = 0; e < kScE; ++e) {
+        if (e * kScT >= w_n) break;  // block-uniform
+        const uint32_t c = cnt[e];
+        unsigned long long tot_packed;
+        const unsigned long long ex = scan_excl<unsigned long long>(
+            (static_cast<unsigned long long>(c) << 13) | (c ? 1u : 0u), s_wt64, &tot_packed);
+        if (c) {
+          const int idx = e * kScT + threadIdx.x;
+          const unsigned long long pre = rec_carry + (ex >> 13);
+          if (pre < kScRound) {
+            const uint32_t pos = pos_carry + static_cast<uint32_t>(ex & 0x1fffu);
+            s_ko[pos] = kov[e];
+            s_delta[pos] = ibv[e] - static_cast<uint32_t>(pre);
+            atomicOr(&bm[pre >> 5], 1u << (pre & 31));
+          }
+          if (pre <= kScRound && pre + c > kScRound) {  // the element holding record kScRound
+            s_next_o = o_cur + idx;
+            s_next_j = static_cast<uint32_t>(kScRound - pre) + (idx == 0 ? j_cur : 0u);
+          }
+        }
+        rec_carry += tot_packed >> 13;
+        pos_carry += static_cast<uint32_t>(tot_packed & 0x1fffu);
+      }
+      const unsigned long long total = rec_carry;
+      const uint32_t n_round = static_cast<uint32_t>(min(static_cast<unsigned long long>(kScRound), total));
+      __syncthreads();
+
+      // ---- 2. generation: records [256 warp, 256 warp + 256) ----
+      uint64_t keys[kScPer];
+      uint32_t rank[kScPer];
+      const uint32_t K0 = (threadIdx.x >> 5) * (kScPer * 32);
+      if (K0 < n_round) {
+        const uint64_t *__restrict__ ikey = u.ikey;
+        // elements starting before K0: popcount of bitmap words [0, K0 / 32)
+        const uint32_t w0 = K0 >> 5;
+        uint32_t c0 = 0;
+#pragma unroll
+        for (int q = 0; q < kScWords / 32; ++q) {
+          const uint32_t wi = static_cast<uint32_t>(lanei + 32 * q);
+          c0 += wi < w0 ? __popc(bm[wi]) : 0u;
+        }
+        uint32_t e_base = __reduce_add_sync(0xffffffffu, c0);
+        // all gathers of the warp's records are issued before the first
+        // shared atomic, so their latencies overlap
+#pragma unroll
+        for (int b = 0; b < kScPer; ++b) {
+          const uint32_t K = K0 + b * 32;
+          const uint32_t word = bm[K >> 5];
+          const uint32_t e = e_base + __popc(word & lemask) - 1u;
+          e_base += __popc(word);
+          const uint32_t k = K + lanei;
+          rank[b] = e;  // element of the record until the rank replaces it
+          // lanes past the round read inner element 0: every address formed
+          // here is inside the inner list whether or not the load is
+          // predicated
+          const uint32_t ii = k < n_round ? s_delta[e] + k : 0u;
+          keys[b] = __ldg(ikey + ii);
+        }
+#pragma unroll
+        for (int b = 0; b < kScPer; ++b) {
+          const uint32_t k = K0 + b * 32 + lanei;
+          if (k < n_round) {
+            const uint64_t key = keys[b] + s_ko[rank[b]];
+            keys[b] = key;
+            rank[b] = atomicAdd(&hist[digit_t<D>(key)], 1u);
+          }
+        }
+      }
+      if (threadIdx.x == 0) {
+        u.o_cur = s_next_o;  // read by the loop test after the barriers below
+        u.j_cur = s_next_j;
+      }
+      __syncthreads();
+
       // ---- 3. digit offsets and one reservation per nonempty digit ----
-      for (int i = threadIdx.x; i < nd; i += kScT) loff[i] = hist[i];
-      __syncthreads();
-      uint32_t tot2;
-      scan_array(loff, nd, s_wt, &tot2);
-      bool ovf = false;
-      for (int gd = threadIdx.x; gd < nd; gd += kScT) {
-        const uint32_t h = hist[gd];
-        if (h) {
-          const uint32_t base = atomicAdd(fill + gd, h);
-          const uint32_t fit = base < cap ? min(h, cap - base) : 0u;
-          ovf |= fit < h;
-          DigitDesc dd;
-          dd.dst = seg0 + (unsigned long long)gd * cap + base - loff[gd];
-          dd.lim = loff[gd] + fit;
-          dd.pad = 0;
-          desc[gd] = dd;
+      {
+        uint32_t hv[pd];
+        uint32_t hsum = 0;
+#pragma unroll
+        for (int q = 0; q < pd; ++q) {
+          const int gd = threadIdx.x * pd + q;
+          hv[q] = gd < nd ? hist[min(gd, nd - 1)] : 0u;
+          hsum += hv[q];
         }
+        // the reservations are issued before the scan, which hides their
+        // latency behind it
+        uint32_t *const fill = u.fill;
+        uint32_t bv[pd];
+#pragma unroll
+        for (int q = 0; q < pd; ++q) bv[q] = hv[q] ? atomicAdd(fill + threadIdx.x * pd + q, hv[q]) : 0u;
+        uint32_t htot;
+        uint32_t o = scan_excl<uint32_t>(hsum, s_wt, &htot);
+        const uint32_t cap = u.cap;
+        const unsigned long long seg0 = u.seg0;
+        bool ovf = false;
+#pragma unroll
+        for (int q = 0; q < pd; ++q) {
+          const int gd = threadIdx.x * pd + q;
+          if (gd < nd) {
+            const uint32_t h = hv[q];
+            loff[gd] = o;
+            hist[gd] = 0;
+            if (h) {
+              const uint32_t base = bv[q];
+              const uint32_t fit = base < cap ? min(h, cap - base) : 0u;
+              ovf |= fit < h;
+              DigitDesc dd;
+              dd.dst = seg0 + (unsigned long long)gd * cap + base - o;
+              dd.lim = o + fit;
+              dd.pad = 0;
+              desc[gd] = dd;
+            }
+            o += h;
+          }
+        }
+        if (ovf) atomicOr(p.overflow + u.inst, 1u);
       }
-      if (ovf) atomicOr(p.overflow + inst_i, 1u);
+      __syncthreads();
       // ---- 4. place by digit, then write the runs ----
       if (K0 < n_round) {
 #pragma unroll
-        for (int b = 0; b < kScBatches; ++b) {
+        for (int b = 0; b < kScPer; ++b) {
           const uint32_t k = K0 + b * 32 + lanei;
           if (k < n_round) sorted[loff[digit_t<D>(keys[b])] + rank[b]] = keys[b];
         }
       }
       __syncthreads();
-      for (uint32_t i = threadIdx.x; i < n_round; i += kScT) {
-        const uint64_t key = sorted[i];
-        const DigitDesc dd = desc[digit_t<D>(key)];
-        if (i < dd.lim) rec[dd.dst + i] = key;
+      {
+        uint64_t *const rec = u.rec;
+#pragma unroll
+        for (int q = 0; q < kScPer; ++q) {
+          const uint32_t i = threadIdx.x + q * kScT;
+          if (i < n_round) {
+            const uint64_t key = sorted[i];
+            const DigitDesc dd = desc[digit_t<D>(key)];
+            if (i < dd.lim) rec[dd.dst + i] = key;
+          }
+        }
       }
       __syncthreads();
     }
@@ -614,7 +685,7 @@ __device__ __forceinline__ void emit(const FastPass &p, bool e, uint64_t key, ui
   }
 }
 
-constexpr int kJS = 11;  // sub-key bits of the in-partition sort
+constexpr int kJS = 12;  // sub-key bits of the in-partition sort (about 2 keys per bucket)
 
 template <int D>
 __global__ void __launch_bounds__(kJT, 1) join_fast_kernel(FastPass p, int nseg) {
@@ -717,7 +788,6 @@ static cudaError_t launch_join_d(const FastPass &p, int nclass_run, cudaStream_t
 }
 
 cudaError_t launch_join_fast(const FastPass &p, int nclass_run, cudaStream_t s) {
-  if (p.S != kJS) return cudaErrorInvalidValue;
   switch (p.D) {
     case 0: return launch_join_d<0>(p, nclass_run, s);
     case 1: return launch_join_d<1>(p, nclass_run, s);

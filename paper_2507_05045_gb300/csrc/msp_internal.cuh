@@ -104,7 +104,7 @@ struct PassDev {
 };
 
 // Streaming pass (fastpath.cu): partitions of fixed capacity <= kFastCap.
-constexpr int kFastCap = 8960;
+constexpr int kFastCap = 8944;
 
 // One instance of a streaming pass (device table; a single solve has one
 // entry, a batch one per instance of the same (m, n)).
@@ -137,6 +137,9 @@ cudaError_t launch_class_sizes(const uint32_t *offO, const uint32_t *offI, uint3
 cudaError_t launch_scatter_fast(const FastPass &p, int nclass_run, cudaStream_t s);
 cudaError_t launch_join_fast(const FastPass &p, int nclass_run, cudaStream_t s);
 size_t scatter_fast_smem(int D);
+// Outer elements per scatter window for an inner list of inner_size
+// elements spread over `classes` buckets.
+int scatter_window(int64_t inner_size, uint32_t classes);
 size_t join_fast_smem(int S);
 
 constexpr int kJoinCap = 6144;   // records per side held in shared memory

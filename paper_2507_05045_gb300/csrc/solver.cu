@@ -58,6 +58,24 @@ Plan make_plan(int m, int n) {
   // classes)
   p.t = p.B <= 8 ? 1 : (p.B <= 18 ? 3 : 4);
   p.t = std::min(p.t, m);
+  // Uneven halves: the inner quarter of each side (Q3 of L, Q4 of R) takes
+  // columns from the outer one until an inner residue bucket holds about 16
+  // elements (2^(q_inner - B)), at most 2^23 of them, so that every outer
+  // element of a scatter window expands to a run of consecutive inner keys.
+  // |L| and |R| do not change, nor do the classes and partitions.
+  for (int side = 0; side < 2; ++side) {
+    const int tot = p.q[side] + p.q[side + 2];
+    const int want = std::min({std::max(p.q[side + 2], p.B + 4), 23, tot - 1});
+    if (want > p.q[side + 2]) {
+      p.q[side + 2] = want;
+      p.q[side] = tot - want;
+    }
+  }
+  c = 0;
+  for (int k = 0; k < 4; ++k) {
+    p.col0[k] = c;
+    c += p.q[k];
+  }
   // streaming pass: partitions of about 2^13 records (512 digits for a
   // class of 2^22); exact two-phase pass: about 2^12 (1024 digits)
   p.D = std::min(12, std::max(0, lgmax - p.B - 13));
@@ -274,8 +292,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     const int64_t per_bucket = std::max<int64_t>(1, in.size / M);
     g.slice_outer = std::max<int64_t>(1, (int64_t(1) << 19) / per_bucket);
     g.slices = static_cast<int>((o.size + g.slice_outer - 1) / g.slice_outer);
-    // a window should cover about two rounds of 4096 records
-    g.wmax = static_cast<int>(std::min<int64_t>(1024, std::max<int64_t>(32, 8192 / per_bucket)));
+    g.wmax = scatter_window(in.size, M);
   }
   // memory budget: free device memory, plus what the stream-ordered pool
   // holds unused from earlier solves, plus this solve's own allocations
