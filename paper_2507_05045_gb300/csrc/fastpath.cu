@@ -28,8 +28,7 @@ namespace {
 
 __device__ __forceinline__ uint32_t lane() { return threadIdx.x & 31; }
 
-// Compile-time digit widths: the top D bits and the next S bits of a key,
-// both inside its high 32-bit word (D + S <= 32).
+// Compile-time digit width: the top D bits of a key.
 template <int D>
 __device__ __forceinline__ uint32_t digit_t(uint64_t key) {
   if constexpr (D == 0) {
@@ -37,12 +36,6 @@ __device__ __forceinline__ uint32_t digit_t(uint64_t key) {
   } else {
     return static_cast<uint32_t>(key >> 32) >> (32 - D);
   }
-}
-
-template <int D, int S>
-__device__ __forceinline__ uint32_t subkey_t(uint64_t key) {
-  static_assert(D + S <= 32, "digit and sub-key must fit the high word");
-  return (static_cast<uint32_t>(key >> 32) >> (32 - D - S)) & ((1u << S) - 1u);
 }
 
 template <typename T>
@@ -70,45 +63,6 @@ __device__ T scan_excl(T v, T *wt, T *total) {
   *total = wt[nw - 1];
   __syncthreads();
   return x + before - v;
-}
-
-// Exclusive scan of a shared array of n entries in place.  Warp w scans the
-// contiguous chunk [w*n/W, (w+1)*n/W) 32 entries at a time with shuffles;
-// the warp totals are scanned by warp 0 and added back.  *total = sum.
-__device__ void scan_array(uint32_t *a, int n, uint32_t *wt, uint32_t *total) {
-  const int ln = lane(), wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int per = (n + nw - 1) / nw;
-  const int b0 = min(wp * per, n), b1 = min(b0 + per, n);
-  uint32_t carry = 0;
-  for (int c = b0; c < b1; c += 32) {
-    const int i = c + ln;
-    const uint32_t v = i < b1 ? a[i] : 0u;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (ln >= o) x += y;
-    }
-    if (i < b1) a[i] = carry + x - v;
-    carry += __shfl_sync(0xffffffffu, x, 31);
-  }
-  if (ln == 0) wt[wp] = carry;
-  __syncthreads();
-  if (wp == 0) {
-    uint32_t t = ln < nw ? wt[ln] : 0u;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-      if (ln >= o) t += y;
-    }
-    if (ln < nw) wt[ln] = t;  // inclusive
-  }
-  __syncthreads();
-  const uint32_t before = wp ? wt[wp - 1] : 0u;
-  if (before)
-    for (int i = b0 + ln; i < b1; i += 32) a[i] += before;
-  *total = wt[nw - 1];
-  __syncthreads();
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -330,6 +284,10 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
     }
     __syncthreads();
 
+    // the first slice of the next window, loaded during the current round
+    bool pf_ok = false;  // block-uniform
+    uint64_t pf_ko = 0;
+    uint32_t pf_cls = 0, pf_ib = 0, pf_c = 0;
     while (u.o_cur < u.o_end) {
       // ---- 1. window: element idx = e * kScT + thread (coalesced) ----
       const long long o_cur = u.o_cur;
@@ -351,10 +309,17 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
           // clamped so that the addresses stay inside the slice for every lane
           const long long o = o_cur + min(idx, w_n - 1);
           if (idx < w_n) {
-            kov[e] = okey[o];
-            const uint32_t w = (r - ocls[o]) & cmask;
-            uint32_t ib = ioff[w];
-            uint32_t c = ioff[w + 1] - ib;
+            uint32_t ib, c;
+            if (e == 0 && pf_ok) {
+              kov[e] = pf_ko;
+              ib = pf_ib;
+              c = pf_c;
+            } else {
+              kov[e] = okey[o];
+              const uint32_t w = (r - ocls[o]) & cmask;
+              ib = ioff[w];
+              c = ioff[w + 1] - ib;
+            }
             if (idx == 0) {
               ib += j_cur;
               c -= j_cur;
@@ -401,6 +366,18 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
       const unsigned long long total = rec_carry;
       const uint32_t n_round = static_cast<uint32_t>(min(static_cast<unsigned long long>(kScRound), total));
       __syncthreads();
+      {
+        // the next window starts at s_next_o: load its first slice now
+        const long long o_nx = s_next_o;
+        const long long o_end = u.o_end;
+        pf_ok = o_nx < o_end;
+        if (pf_ok) {
+          const int wn_nx = static_cast<int>(min(static_cast<long long>(u.wmax), o_end - o_nx));
+          const long long o = o_nx + min(static_cast<int>(threadIdx.x), wn_nx - 1);
+          pf_ko = u.okey[o];
+          pf_cls = u.ocls[o];
+        }
+      }
 
       // ---- 2. generation: records [256 warp, 256 warp + 256) ----
       uint64_t keys[kScPer];
@@ -443,15 +420,23 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
           }
         }
       }
+      if (pf_ok) {  // bucket of the prefetched elements
+        const uint32_t w = (u.r - pf_cls) & p.cmask;
+        pf_ib = u.ioff[w];
+        pf_c = u.ioff[w + 1] - pf_ib;
+      }
       if (threadIdx.x == 0) {
         u.o_cur = s_next_o;  // read by the loop test after the barriers below
         u.j_cur = s_next_j;
       }
       __syncthreads();
 
-      // ---- 3. digit offsets and one reservation per nonempty digit ----
+      // ---- 3. digit offsets; one reservation per nonempty digit ----
+      // The reservations are issued first; their results are needed only for
+      // the run descriptors, which are formed after the placement, so the
+      // atomics' latency hides behind the scan and the placement.
+      uint32_t hv[pd], bv[pd], ov[pd];
       {
-        uint32_t hv[pd];
         uint32_t hsum = 0;
 #pragma unroll
         for (int q = 0; q < pd; ++q) {
@@ -459,47 +444,51 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
           hv[q] = gd < nd ? hist[min(gd, nd - 1)] : 0u;
           hsum += hv[q];
         }
-        // the reservations are issued before the scan, which hides their
-        // latency behind it
         uint32_t *const fill = u.fill;
-        uint32_t bv[pd];
 #pragma unroll
         for (int q = 0; q < pd; ++q) bv[q] = hv[q] ? atomicAdd(fill + threadIdx.x * pd + q, hv[q]) : 0u;
         uint32_t htot;
         uint32_t o = scan_excl<uint32_t>(hsum, s_wt, &htot);
-        const uint32_t cap = u.cap;
-        const unsigned long long seg0 = u.seg0;
-        bool ovf = false;
 #pragma unroll
         for (int q = 0; q < pd; ++q) {
           const int gd = threadIdx.x * pd + q;
+          ov[q] = o;
           if (gd < nd) {
-            const uint32_t h = hv[q];
             loff[gd] = o;
             hist[gd] = 0;
-            if (h) {
-              const uint32_t base = bv[q];
-              const uint32_t fit = base < cap ? min(h, cap - base) : 0u;
-              ovf |= fit < h;
-              DigitDesc dd;
-              dd.dst = seg0 + (unsigned long long)gd * cap + base - o;
-              dd.lim = o + fit;
-              dd.pad = 0;
-              desc[gd] = dd;
-            }
-            o += h;
           }
+          o += hv[q];
         }
-        if (ovf) atomicOr(p.overflow + u.inst, 1u);
       }
       __syncthreads();
-      // ---- 4. place by digit, then write the runs ----
+      // ---- 4. place by digit, form the run descriptors, write the runs ----
       if (K0 < n_round) {
 #pragma unroll
         for (int b = 0; b < kScPer; ++b) {
           const uint32_t k = K0 + b * 32 + lanei;
           if (k < n_round) sorted[loff[digit_t<D>(keys[b])] + rank[b]] = keys[b];
         }
+      }
+      {
+        const uint32_t cap = u.cap;
+        const unsigned long long seg0 = u.seg0;
+        bool ovf = false;
+#pragma unroll
+        for (int q = 0; q < pd; ++q) {
+          const int gd = threadIdx.x * pd + q;
+          const uint32_t h = hv[q];
+          if (gd < nd && h) {
+            const uint32_t base = bv[q];
+            const uint32_t fit = base < cap ? min(h, cap - base) : 0u;
+            ovf |= fit < h;
+            DigitDesc dd;
+            dd.dst = seg0 + (unsigned long long)gd * cap + base - ov[q];
+            dd.lim = ov[q] + fit;
+            dd.pad = 0;
+            desc[gd] = dd;
+          }
+        }
+        if (ovf) atomicOr(p.overflow + u.inst, 1u);
       }
       __syncthreads();
       {
@@ -569,20 +558,35 @@ cudaError_t launch_scatter_fast(const FastPass &p, int nclass_run, cudaStream_t 
 
 // -------------------------------------------------------------------------
 // Join (S4 second digit + S5).  Persistent, one block of 1024 threads per SM.
-// Partition s = (class, digit): the left keys arrive by cp.async.bulk into
-// one of two buffers (the next partition's left side streams in while this
-// one is processed), the right keys into a third buffer.  The left side is
-// counting-sorted in place by the next S key bits; every right key probes
-// its bucket.  The first left element equal to the key is claimed with a
-// shared bit (so duplicate right keys emit once) and the (class, key) pair
-// is appended with one atomic per warp.
+// Partition s = (class, digit).  The left keys arrive by cp.async.bulk into
+// a shared buffer one partition ahead and are hashed into a shared table of
+// 4096 buckets (the 12 key bits below the digit) with 8 slots each; a slot
+// holds an 18-bit fingerprint (the next key bits) and the key's index in the
+// partition, a bucket past 8 keys spills into a short overflow list.  The
+// right keys are read straight from device memory with coalesced 128-bit
+// loads into registers (each is used once) and probe their bucket: one
+// 128-bit shared load and four fingerprint compares for most buckets.  A
+// fingerprint hit is confirmed against the full left key in device memory;
+// the smallest index of an equal left key is claimed with a shared bit (so
+// duplicate right keys emit once) and the (class, key) pair is appended
+// with one atomic per warp.
 // -------------------------------------------------------------------------
-constexpr int kJT = 1024;
-constexpr int kJReg = (kFastCap + kJT - 1) / kJT;
+constexpr int kJT = 512;                    // threads per block, two blocks per SM
+constexpr int kJBits = 11;                  // buckets of the probe table
+constexpr int kJBuckets = 1 << kJBits;
+constexpr int kJSlots = 8;                  // slots per bucket
+constexpr int kJOvf = 512;                  // overflow entries (bucket << 16 | index)
+constexpr int kJPairs = (kFastCap / 2 + kJT - 1) / kJT;  // 128-bit right loads per thread
+static_assert(kFastCap <= 65536, "16-bit slot indices");
+static_assert(kFastCap % 16 == 0, "partitions are 16-record multiples");
 
-size_t join_fast_smem(int S) {
-  return 3 * (size_t)kFastCap * sizeof(uint64_t) + (((size_t)1 << S) + 1) * sizeof(uint32_t) +
-         (kFastCap / 32 + 1) * sizeof(uint32_t) + 64;
+size_t join_fast_smem() {
+  return (size_t)kFastCap * sizeof(uint64_t)                    // left keys (bulk copy target)
+         + (size_t)kJBuckets * kJSlots * sizeof(uint16_t) * 2  // slot fingerprints, slot indices
+         + (size_t)kJBuckets * sizeof(uint32_t)                // bucket fill
+         + (size_t)(kFastCap / 32 + 1) * sizeof(uint32_t)      // claim bits
+         + (size_t)kJOvf * sizeof(uint32_t)                    // overflow list
+         + 64;
 }
 
 struct SegRef {
@@ -645,30 +649,6 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, unsig
   return true;
 }
 
-template <int D, int S>
-__device__ void sort_in_place(uint64_t *buf, uint32_t n, uint32_t *off, uint32_t *wt) {
-  constexpr int nb = 1 << S;
-  uint64_t k[kJReg];
-  uint32_t rk[kJReg];
-#pragma unroll
-  for (int q = 0; q < kJReg; ++q) {
-    const uint32_t i = threadIdx.x + q * kJT;
-    if (i < n) {
-      k[q] = buf[i];
-      rk[q] = atomicAdd(&off[subkey_t<D, S>(k[q])], 1u);
-    }
-  }
-  __syncthreads();
-  uint32_t tot;
-  scan_array(off, nb, wt, &tot);
-  if (threadIdx.x == 0) off[nb] = tot;
-#pragma unroll
-  for (int q = 0; q < kJReg; ++q) {
-    const uint32_t i = threadIdx.x + q * kJT;
-    if (i < n) buf[off[subkey_t<D, S>(k[q])] + rk[q]] = k[q];
-  }
-}
-
 __device__ __forceinline__ void emit(const FastPass &p, bool e, uint64_t key, uint32_t cls) {
   const unsigned bal = __ballot_sync(0xffffffffu, e);
   if (!bal) return;
@@ -685,103 +665,174 @@ __device__ __forceinline__ void emit(const FastPass &p, bool e, uint64_t key, ui
   }
 }
 
-constexpr int kJS = 12;  // sub-key bits of the in-partition sort (about 2 keys per bucket)
+// Bucket and fingerprint of a key: the kJBits bits below the top D (digit)
+// bits, then 16 more; fingerprint 0 marks an empty slot, so a key whose 16
+// bits are 0 uses 1.
+template <int D>
+__device__ __forceinline__ uint32_t jbucket(uint64_t key) {
+  return static_cast<uint32_t>(key >> (64 - D - kJBits)) & (kJBuckets - 1u);
+}
+template <int D>
+__device__ __forceinline__ uint32_t jfp(uint64_t key) {
+  static_assert(D + kJBits + 16 <= 64, "fingerprint must fit below the digit");
+  const uint32_t f = static_cast<uint32_t>(key >> (64 - D - kJBits - 16)) & 0xffffu;
+  return f ? f : 1u;
+}
+
+// Nonzero when some 16-bit half of x is zero.
+__device__ __forceinline__ uint32_t zero_half(uint32_t x) { return (x - 0x00010001u) & ~x & 0x80008000u; }
+
+// Probe one right key.  Returns true when this lane claimed the lowest index
+// of a left key equal to it.
+template <int D>
+__device__ __forceinline__ bool probe(uint64_t key, const uint64_t *__restrict__ Lg, const uint16_t *fps,
+                                      const uint16_t *idxs, const uint32_t *cnt, const uint32_t *ovf,
+                                      uint32_t n_ovf, uint32_t *flags) {
+  const uint32_t b = jbucket<D>(key);
+  const uint32_t fp = jfp<D>(key);
+  const uint4 w = *reinterpret_cast<const uint4 *>(fps + b * kJSlots);
+  const uint32_t f2 = fp * 0x00010001u;
+  const uint32_t any = zero_half(w.x ^ f2) | zero_half(w.y ^ f2) | zero_half(w.z ^ f2) | zero_half(w.w ^ f2);
+  const uint32_t c = cnt[b];
+  if (!any && c <= kJSlots) return false;
+  uint32_t best = 0xffffffffu;
+  const uint32_t n = min(c, static_cast<uint32_t>(kJSlots));
+  for (uint32_t j = 0; j < n; ++j) {
+    if (fps[b * kJSlots + j] == fp) {
+      const uint32_t idx = idxs[b * kJSlots + j];
+      if (idx < best && Lg[idx] == key) best = idx;
+    }
+  }
+  if (c > kJSlots) {
+    for (uint32_t j = 0; j < n_ovf; ++j) {
+      const uint32_t v = ovf[j];
+      if ((v >> 16) == b) {
+        const uint32_t idx = v & 0xffffu;
+        if (idx < best && Lg[idx] == key) best = idx;
+      }
+    }
+  }
+  if (best == 0xffffffffu) return false;
+  const uint32_t bit = 1u << (best & 31);
+  return (atomicOr(&flags[best >> 5], bit) & bit) == 0;
+}
 
 template <int D>
-__global__ void __launch_bounds__(kJT, 1) join_fast_kernel(FastPass p, int nseg) {
+__global__ void __launch_bounds__(kJT, 2) join_fast_kernel(FastPass p, int nseg) {
   extern __shared__ __align__(16) uint8_t sm[];
-  uint64_t *const bufL0 = reinterpret_cast<uint64_t *>(sm);  // two left buffers
-  uint64_t *const bufR = bufL0 + 2 * kFastCap;
-  constexpr int S = kJS;
-  constexpr int nb = 1 << S;
-  uint32_t *off = reinterpret_cast<uint32_t *>(bufR + kFastCap);
-  uint32_t *flags = off + nb + 1;
-  const int nflag = kFastCap / 32 + 1;
-  __shared__ __align__(8) uint64_t barL[2];
-  __shared__ __align__(8) uint64_t barR;
-  __shared__ uint32_t s_wt[32];
+  uint64_t *const bufL = reinterpret_cast<uint64_t *>(sm);
+  uint16_t *const fps = reinterpret_cast<uint16_t *>(bufL + kFastCap);
+  uint16_t *const idxs = fps + kJBuckets * kJSlots;
+  uint32_t *const cnt = reinterpret_cast<uint32_t *>(idxs + kJBuckets * kJSlots);
+  uint32_t *const flags = cnt + kJBuckets;
+  uint32_t *const ovf = flags + (kFastCap / 32 + 1);
+  constexpr int nflag = kFastCap / 32 + 1;
+  constexpr int nfp16 = kJBuckets * kJSlots / 8;  // fingerprint table in 16-byte words
+  __shared__ __align__(8) uint64_t barL;
+  __shared__ uint32_t s_novf;
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
-    mbar_init(&barL[0], 1);
-    mbar_init(&barL[1], 1);
-    mbar_init(&barR, 1);
+    mbar_init(&barL, 1);
+    s_novf = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  for (int i = threadIdx.x; i < kJBuckets; i += kJT) cnt[i] = 0;
+  for (int i = threadIdx.x; i < nflag; i += kJT) flags[i] = 0;
+  for (int i = threadIdx.x; i < nfp16; i += kJT) reinterpret_cast<uint4 *>(fps)[i] = make_uint4(0, 0, 0, 0);
   __syncthreads();
   const int G = gridDim.x;
   int s = blockIdx.x;
   if (s < nseg && threadIdx.x == 0) {
     const SegRef r0 = seg_ref(p, s);
-    issue_keys(r0.L, r0.nL, bufL0, &barL[0]);
-    issue_keys(r0.R, r0.nR, bufR, &barR);
+    issue_keys(r0.L, r0.nL, bufL, &barL);
   }
-  uint32_t phL = 0, phR = 0;  // bit st of phL: parity of left buffer st
-  for (int k = 0; s < nseg; ++k, s += G) {
-    const int st = k & 1;
+  uint32_t phL = 0;
+  for (; s < nseg; s += G) {
     const SegRef r = seg_ref(p, s);
+    // right keys of this partition: coalesced 128-bit loads into registers,
+    // in flight while the left side is hashed
+    ulonglong2 rk[kJPairs];
+    const uint32_t npair = (r.nR + 1u) >> 1;
+#pragma unroll
+    for (int q = 0; q < kJPairs; ++q) {
+      const uint32_t pi = threadIdx.x + q * kJT;
+      // clamped: every address formed is inside the partition
+      const uint32_t pc = npair ? min(pi, npair - 1u) : 0u;
+      rk[q] = npair ? __ldg(reinterpret_cast<const ulonglong2 *>(r.R) + pc) : make_ulonglong2(0, 0);
+    }
+    if (!wait_phase(&barL, phL, p.error, &s_ok)) return;
+    phL ^= 1u;
+    // hash the left side
+    for (uint32_t i = threadIdx.x; i < r.nL; i += kJT) {
+      const uint64_t key = bufL[i];
+      const uint32_t b = jbucket<D>(key);
+      const uint32_t slot = atomicAdd(&cnt[b], 1u);
+      if (slot < kJSlots) {
+        fps[b * kJSlots + slot] = static_cast<uint16_t>(jfp<D>(key));
+        idxs[b * kJSlots + slot] = static_cast<uint16_t>(i);
+      } else {
+        const uint32_t o = atomicAdd(&s_novf, 1u);
+        if (o < kJOvf) ovf[o] = (b << 16) | i;
+      }
+    }
+    __syncthreads();
     const int sn = s + G;
     if (sn < nseg && threadIdx.x == 0) {
       fence_proxy_async();
       const SegRef rn = seg_ref(p, sn);
-      issue_keys(rn.L, rn.nL, bufL0 + (st ^ 1) * kFastCap, st ? &barL[0] : &barL[1]);
+      issue_keys(rn.L, rn.nL, bufL, &barL);
     }
-    for (int i = threadIdx.x; i <= nb; i += kJT) off[i] = 0;
-    for (int i = threadIdx.x; i < nflag; i += kJT) flags[i] = 0;
-    if (!wait_phase(st ? &barL[1] : &barL[0], (phL >> st) & 1u, p.error, &s_ok)) return;
-    phL ^= 1u << st;
-    uint64_t *bL = bufL0 + st * kFastCap;
-    if (r.nL) sort_in_place<D, S>(bL, r.nL, off, s_wt);
-    if (!wait_phase(&barR, phR, p.error, &s_ok)) return;  // includes a block barrier
-    phR ^= 1u;
-    if (r.nR) {
-      const uint32_t cls = r.cls;
-      const uint32_t rounds = (r.nR + kJT - 1) / kJT;
-      for (uint32_t rd = 0; rd < rounds; ++rd) {
-        const uint32_t i = rd * kJT + threadIdx.x;
-        bool e = false;
-        uint64_t key = 0;
-        if (i < r.nR) {
-          key = bufR[i];
-          const uint32_t b = subkey_t<D, S>(key);
-          const uint32_t je = off[b + 1];
-          for (uint32_t j = off[b]; j < je; ++j) {
-            if (bL[j] == key) {
-              const uint32_t bit = 1u << (j & 31);
-              e = (atomicOr(&flags[j >> 5], bit) & bit) == 0;
-              break;
-            }
-          }
+    const uint32_t n_ovf = s_novf;
+    if (n_ovf > kJOvf) {
+      // more spilled keys than the list holds: the instance's pass is re-run
+      // on the exact path
+      if (threadIdx.x == 0) atomicOr(p.overflow + s / (p.nclass << p.D), 1u);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kJPairs; ++q) {
+        const uint32_t pi = threadIdx.x + q * kJT;
+        if (q * kJT < static_cast<int>(npair)) {  // block-uniform: bounds the emit calls
+          const bool v0 = 2 * pi < r.nR, v1 = 2 * pi + 1 < r.nR;
+          const bool e0 = v0 && probe<D>(rk[q].x, r.L, fps, idxs, cnt, ovf, n_ovf, flags);
+          emit(p, e0, rk[q].x, r.cls);
+          const bool e1 = v1 && probe<D>(rk[q].y, r.L, fps, idxs, cnt, ovf, n_ovf, flags);
+          emit(p, e1, rk[q].y, r.cls);
         }
-        emit(p, e, key, cls);
       }
     }
     __syncthreads();
-    if (sn < nseg && threadIdx.x == 0) {
-      fence_proxy_async();
-      const SegRef rn = seg_ref(p, sn);
-      issue_keys(rn.R, rn.nR, bufR, &barR);
-    }
+    for (int i = threadIdx.x; i < kJBuckets; i += kJT) cnt[i] = 0;
+    for (int i = threadIdx.x; i < nflag; i += kJT) flags[i] = 0;
+    for (int i = threadIdx.x; i < nfp16; i += kJT) reinterpret_cast<uint4 *>(fps)[i] = make_uint4(0, 0, 0, 0);
+    if (threadIdx.x == 0) s_novf = 0;
+    // the next wait_phase begins with a block barrier
   }
 }
 
 template <int D>
 static cudaError_t launch_join_d(const FastPass &p, int nclass_run, cudaStream_t s) {
   static size_t attr = 0;
-  static int sms = 0;
-  const size_t smem = join_fast_smem(kJS);
+  static int sms = 0, per_sm = 0;
+  const size_t smem = join_fast_smem();
   if (smem > attr) {
     cudaError_t e = cudaFuncSetAttribute(join_fast_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     attr = smem;
-    int dev = 0;
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, join_fast_kernel<D>, kJT, smem) != cudaSuccess ||
+        n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    per_sm = n;
   }
   FastPass q = p;
   q.nclass = nclass_run;
   const int nseg = p.ninst * (nclass_run << D);
-  const int blocks = std::min(nseg, sms);
+  const int blocks = std::min(nseg, per_sm * sms);
   if (blocks < 1) return cudaSuccess;
   join_fast_kernel<D><<<blocks, kJT, smem, s>>>(q, nseg);
   return cudaGetLastError();

@@ -104,7 +104,7 @@ struct PassDev {
 };
 
 // Streaming pass (fastpath.cu): partitions of fixed capacity <= kFastCap.
-constexpr int kFastCap = 8944;
+constexpr int kFastCap = 4608;
 
 // One instance of a streaming pass (device table; a single solve has one
 // entry, a batch one per instance of the same (m, n)).
@@ -140,7 +140,7 @@ size_t scatter_fast_smem(int D);
 // Outer elements per scatter window for an inner list of inner_size
 // elements spread over `classes` buckets.
 int scatter_window(int64_t inner_size, uint32_t classes);
-size_t join_fast_smem(int S);
+size_t join_fast_smem();
 
 constexpr int kJoinCap = 6144;   // records per side held in shared memory
 constexpr int kJoinThreads = 512;

@@ -49,9 +49,8 @@ Plan make_plan(int m, int n) {
   p.lgL = p.q[0] + p.q[2];
   p.lgR = p.q[1] + p.q[3];
   const int lgmax = std::max(p.lgL, p.lgR);
-  // about 2^22 records per class and side, partitions of about 2^12
-  // (1024 digits); the exact class-size convolution needs 2^B <= 2^18.
-  p.B = std::min(23, std::max(0, lgmax - 22));
+  // about 2^21 records per class and side (at most 2^23 classes)
+  p.B = std::min(23, std::max(0, lgmax - 21));
   // row 1 alone while its residues stay uniform (2^B <= 256 against a
   // row-1 spread of a few hundred); three rows beyond, which keeps the class
   // sizes within about one percent of each other (four rows past 2^18
@@ -76,9 +75,9 @@ Plan make_plan(int m, int n) {
     p.col0[k] = c;
     c += p.q[k];
   }
-  // streaming pass: partitions of about 2^13 records (512 digits for a
-  // class of 2^22); exact two-phase pass: about 2^12 (1024 digits)
-  p.D = std::min(12, std::max(0, lgmax - p.B - 13));
+  // partitions of about 2^12 records (512 digits for a class of 2^21),
+  // in the streaming and in the exact two-phase pass
+  p.D = std::min(12, std::max(0, lgmax - p.B - 12));
   p.Dx = std::min(12, std::max(0, lgmax - p.B - 12));
   p.S = 11;  // 2048 shared-memory buckets per partition side
   uint64_t s = 0x2507050450000001ull;
