@@ -52,11 +52,14 @@ def parse():
     ap.add_argument("--m", type=int, default=M_)
     ap.add_argument("--n", type=int, default=N_)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", choices=["9_80", "batch_6_50", "serving", "10_90_part"], default="9_80",
+    ap.add_argument("--config", choices=["9_80", "batch_6_50", "serving", "10_90_part", "profile_part"],
+                    default="9_80",
                     help="9_80 (default): the headline exhaustive solve; batch_6_50: 64 (6,50) "
                          "instances in one batched call vs one at a time; serving: the mixed Poisson "
                          "request stream through the server vs sequential solving; 10_90_part: one "
-                         "seeded 1/64 of the residue classes of a (10,90) instance")
+                         "seeded 1/64 of the residue classes of a (10,90) instance; profile_part: "
+                         "the small case the ncu captures use (the (9,80) instance of the default "
+                         "workload over 1/4096 of its residue classes, 1500 MB budget, one solve)")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--rate-factor", type=float, default=0.8)
     return ap.parse_args()
@@ -516,6 +519,25 @@ def bench_10_90(args):
            "kernels": st["kernels"]})
 
 
+def bench_profile_part(args):
+    """One solve of the (9,80) bench instance over residue-class part 0 of
+    4096 with a 1500 MB device budget: a few passes of a few hundred MB, the
+    case the ncu captures under profiles/ are taken on."""
+    import paper_2507_05045_gb300 as msp
+    from paper_2507_05045_gb300 import build
+    build.build()
+    A, d, _ = mi.generate(M_, N_, SEED)
+    with msp.Instance(A, d, class_part=(0, 4096), memory_budget=1500 << 20, profiling=True) as inst:
+        t0 = time.perf_counter()
+        inst.solve_all()
+        dt = time.perf_counter() - t0
+        st = inst.stats()
+    _emit({"config": {"workload": f"({M_},{N_}) plain instance seed {SEED}, classes part 0 of 4096, "
+                                  "1500 MB budget"},
+           "seconds": dt, "passes": st["passes"], "records_done": st["records_done"],
+           "class_bits": st["class_bits"], "digit_bits": st["digit_bits"], "kernels": st["kernels"]})
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_init(args)
@@ -531,6 +553,9 @@ def main():
         elif args.config == "10_90_part":
             if rank == 0:
                 bench_10_90(args)
+        elif args.config == "profile_part":
+            if rank == 0:
+                bench_profile_part(args)
         else:
             native(args, world, rank, local, pg)
     finally:
