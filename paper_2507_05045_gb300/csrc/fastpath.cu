@@ -191,8 +191,8 @@ constexpr int kScWords = kScRound / 32;     // bitmap words
 static_assert(kScW <= kScRound, "compacted elements must fit the window arrays");
 
 struct __align__(16) DigitDesc {
-  unsigned long long dst;  // record index of sorted position 0 of this digit's run
-  uint32_t lim;            // sorted positions below lim are inside the partition
+  uint64_t *dst;  // where sorted position 0 of this digit's run would go
+  uint32_t lim;   // sorted positions below lim are inside the partition
   uint32_t pad;
 };
 
@@ -232,7 +232,7 @@ template <int D>
 __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPass p, int nwu) {
   extern __shared__ __align__(16) uint8_t sm[];
   constexpr int nd = 1 << D;
-  constexpr int pd = nd > kScT ? nd / kScT : 1;  // digits per thread in the digit phase
+  constexpr int pd = (nd + kScT - 1) / kScT;  // digits per thread in the digit phase
   uint64_t *const s_ko = reinterpret_cast<uint64_t *>(sm);            // window: outer key of element e
   uint64_t *const sorted = s_ko;                                      // placement: keys by digit
   uint32_t *const s_delta = reinterpret_cast<uint32_t *>(s_ko + kScRound);
@@ -240,7 +240,6 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
   uint32_t *const hist = reinterpret_cast<uint32_t *>(desc + nd);
   uint32_t *const loff = hist + nd;
   uint32_t *const bm = loff + nd;
-  __shared__ unsigned long long s_wt64[32];
   __shared__ uint32_t s_wt[32];
   __shared__ ScatterUnit u;
   __shared__ long long s_next_o;
@@ -334,23 +333,27 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
         s_next_o = o_cur + w_n;
         s_next_j = 0;
       }
-      // Element slices in order; a scan per slice (records in the high bits,
-      // nonempty elements in the low 13) gives each element its first record
-      // and its compacted position.
+      // Element slices in order; a 32-bit scan per slice (records in the
+      // high 22 bits, nonempty elements in the low 10) gives each element its
+      // first record and its compacted position.  Counts enter the scan
+      // clamped to kScRound + 1: every prefix that decides something (a
+      // first record below kScRound, the element holding record kScRound,
+      // the round's total when it is at most kScRound) is then exact.
+      static_assert(kScT <= 1024 && kScT * (kScRound + 1) < (1u << 22), "packed window scan");
       unsigned long long rec_carry = 0;
       uint32_t pos_carry = 0;
 #pragma unroll
       for (int e = 0; e < kScE; ++e) {
         if (e * kScT >= w_n) break;  // block-uniform
         const uint32_t c = cnt[e];
-        unsigned long long tot_packed;
-        const unsigned long long ex = scan_excl<unsigned long long>(
-            (static_cast<unsigned long long>(c) << 13) | (c ? 1u : 0u), s_wt64, &tot_packed);
+        const uint32_t cc = min(c, static_cast<uint32_t>(kScRound + 1));
+        uint32_t tot_packed;
+        const uint32_t ex = scan_excl<uint32_t>((cc << 10) | (c ? 1u : 0u), s_wt, &tot_packed);
         if (c) {
           const int idx = e * kScT + threadIdx.x;
-          const unsigned long long pre = rec_carry + (ex >> 13);
+          const unsigned long long pre = rec_carry + (ex >> 10);
           if (pre < kScRound) {
-            const uint32_t pos = pos_carry + static_cast<uint32_t>(ex & 0x1fffu);
+            const uint32_t pos = pos_carry + (ex & 0x3ffu);
             s_ko[pos] = kov[e];
             s_delta[pos] = ibv[e] - static_cast<uint32_t>(pre);
             atomicOr(&bm[pre >> 5], 1u << (pre & 31));
@@ -360,8 +363,8 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
             s_next_j = static_cast<uint32_t>(kScRound - pre) + (idx == 0 ? j_cur : 0u);
           }
         }
-        rec_carry += tot_packed >> 13;
-        pos_carry += static_cast<uint32_t>(tot_packed & 0x1fffu);
+        rec_carry += tot_packed >> 10;
+        pos_carry += tot_packed & 0x3ffu;
       }
       const unsigned long long total = rec_carry;
       const uint32_t n_round = static_cast<uint32_t>(min(static_cast<unsigned long long>(kScRound), total));
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
         const uint32_t w0 = K0 >> 5;
         uint32_t c0 = 0;
 #pragma unroll
-        for (int q = 0; q < kScWords / 32; ++q) {
+        for (int q = 0; q < (kScWords + 31) / 32; ++q) {
           const uint32_t wi = static_cast<uint32_t>(lanei + 32 * q);
           c0 += wi < w0 ? __popc(bm[wi]) : 0u;
         }
@@ -482,7 +485,8 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
             const uint32_t fit = base < cap ? min(h, cap - base) : 0u;
             ovf |= fit < h;
             DigitDesc dd;
-            dd.dst = seg0 + (unsigned long long)gd * cap + base - ov[q];
+            // may point before the partition; only positions from ov[q] on are used
+            dd.dst = u.rec + (seg0 + (unsigned long long)gd * cap + base - ov[q]);
             dd.lim = ov[q] + fit;
             dd.pad = 0;
             desc[gd] = dd;
@@ -491,16 +495,13 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
         if (ovf) atomicOr(p.overflow + u.inst, 1u);
       }
       __syncthreads();
-      {
-        uint64_t *const rec = u.rec;
 #pragma unroll
-        for (int q = 0; q < kScPer; ++q) {
-          const uint32_t i = threadIdx.x + q * kScT;
-          if (i < n_round) {
-            const uint64_t key = sorted[i];
-            const DigitDesc dd = desc[digit_t<D>(key)];
-            if (i < dd.lim) rec[dd.dst + i] = key;
-          }
+      for (int q = 0; q < kScPer; ++q) {
+        const uint32_t i = threadIdx.x + q * kScT;
+        if (i < n_round) {
+          const uint64_t key = sorted[i];
+          const DigitDesc dd = desc[digit_t<D>(key)];
+          if (i < dd.lim) dd.dst[i] = key;
         }
       }
       __syncthreads();
