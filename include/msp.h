@@ -137,7 +137,27 @@ MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
  *                       is the full solution set, so parts can be solved by
  *                       different processes or GPUs, or one part timed to
  *                       project the full time (records_done / all records). */
-enum { MSP_OPT_EXACT_PATH = 1, MSP_OPT_CLASS_PART = 2, MSP_OPT_CLASS_PARTS = 3 };
+/*   MSP_OPT_CLASS_BITS   residue classes 2^B of the plan, B in [0, 23]
+ *   MSP_OPT_DIGIT_BITS   radix digit bits D of the streaming pass, in [0, 12]
+ *                        (partitions of about |L| / 2^(B + D) records; a class
+ *                        whose partitions would not fit shared memory is
+ *                        solved on the exact path)
+ *   MSP_OPT_INNER_BITS   the inner quarter of each side (Q3 of L, Q4 of R)
+ *                        gets B + value columns (at most 23, never fewer than
+ *                        the even split), so an inner residue bucket holds
+ *                        about 2^value elements: the run of records one outer
+ *                        element expands to in the scatter, in [0, 12]
+ *                        For these three, -1 (the default) restores the
+ *                        built-in formula; any choice gives the same solutions.
+ *                        They are what the package's autotuner sets per (m, n). */
+enum {
+  MSP_OPT_EXACT_PATH = 1,
+  MSP_OPT_CLASS_PART = 2,
+  MSP_OPT_CLASS_PARTS = 3,
+  MSP_OPT_CLASS_BITS = 4,
+  MSP_OPT_DIGIT_BITS = 5,
+  MSP_OPT_INNER_BITS = 6
+};
 MSP_API int msp_set_option(msp_instance *inst, int option, int64_t value);
 
 /* Time every kernel launch of later solves with CUDA events (on = 1). */
@@ -199,6 +219,10 @@ MSP_API const char *msp_last_error(void);
 
 /* Library version string. */
 MSP_API const char *msp_version(void);
+
+/* Name of the calling thread's current CUDA device ("" when there is none);
+ * the autotuner keys its cache by it. */
+MSP_API const char *msp_device_name(void);
 
 #ifdef __cplusplus
 }

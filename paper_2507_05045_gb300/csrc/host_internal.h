@@ -23,6 +23,7 @@ struct msp_instance {
   bool profiling = false;
   bool force_exact = false;
   int64_t part = 0, parts = 1;  // residue-class subset [part*M/parts, (part+1)*M/parts)
+  int plan_B = -1, plan_D = -1, plan_inner = -1;  // plan overrides (-1 = formula)
 };
 
 namespace msp {
@@ -37,7 +38,13 @@ struct Plan {
   uint64_t w_row[kMaxRows];
 };
 
-Plan make_plan(int m, int n);
+// Plan choices that override the formulas of make_plan (-1 = formula):
+// class bits B (residue modulus 2^B), digit bits D of the streaming pass,
+// inner bits (the inner quarter of each side gets B + inner bits columns).
+struct PlanChoice {
+  int B = -1, D = -1, inner = -1;
+};
+Plan make_plan(int m, int n, const PlanChoice &ch = PlanChoice());
 // Argument checks shared by the entry points (MSP_OK or an error status).
 int validate(const int32_t *A, const int32_t *d, int m, int n);
 // K(v) and kappa(v) of a vector of row sums under a plan.

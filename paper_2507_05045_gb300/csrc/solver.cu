@@ -35,7 +35,7 @@ static uint64_t splitmix(uint64_t &s) {
 
 // Quarters: sizes ceil(n/4) for the first n mod 4 quarters, floor(n/4) for
 // the rest; L pairs the largest quarter Q1 with Q3, R pairs Q2 with Q4.
-Plan make_plan(int m, int n) {
+Plan make_plan(int m, int n, const PlanChoice &ch) {
   Plan p{};
   p.m = m;
   p.n = n;
@@ -50,7 +50,7 @@ Plan make_plan(int m, int n) {
   p.lgR = p.q[1] + p.q[3];
   const int lgmax = std::max(p.lgL, p.lgR);
   // about 2^21 records per class and side (at most 2^23 classes)
-  p.B = std::min(23, std::max(0, lgmax - 21));
+  p.B = ch.B >= 0 ? std::min(23, ch.B) : std::min(23, std::max(0, lgmax - 21));
   // row 1 alone while its residues stay uniform (2^B <= 256 against a
   // row-1 spread of a few hundred); three rows beyond, which keeps the class
   // sizes within about one percent of each other (four rows past 2^18
@@ -62,9 +62,10 @@ Plan make_plan(int m, int n) {
   // elements (2^(q_inner - B)), at most 2^23 of them, so that every outer
   // element of a scatter window expands to a run of consecutive inner keys.
   // |L| and |R| do not change, nor do the classes and partitions.
+  const int inner_bits = ch.inner >= 0 ? ch.inner : 4;
   for (int side = 0; side < 2; ++side) {
     const int tot = p.q[side] + p.q[side + 2];
-    const int want = std::min({std::max(p.q[side + 2], p.B + 4), 23, tot - 1});
+    const int want = std::min({std::max(p.q[side + 2], p.B + inner_bits), 23, tot - 1});
     if (want > p.q[side + 2]) {
       p.q[side + 2] = want;
       p.q[side] = tot - want;
@@ -77,7 +78,7 @@ Plan make_plan(int m, int n) {
   }
   // partitions of about 2^12 records (512 digits for a class of 2^21),
   // in the streaming and in the exact two-phase pass
-  p.D = std::min(12, std::max(0, lgmax - p.B - 12));
+  p.D = ch.D >= 0 ? std::min(12, ch.D) : std::min(12, std::max(0, lgmax - p.B - 12));
   p.Dx = std::min(12, std::max(0, lgmax - p.B - 12));
   p.S = 11;  // 2048 shared-memory buckets per partition side
   uint64_t s = 0x2507050450000001ull;
@@ -134,7 +135,11 @@ struct SolveResult {
 // The solve proper.  `out` receives unsorted solution masks (two words each).
 int solve_impl(msp_instance *inst, SolveResult *res) {
   const int m = inst->m, n = inst->n;
-  const Plan p = make_plan(m, n);
+  PlanChoice ch;
+  ch.B = inst->plan_B;
+  ch.D = inst->plan_D;
+  ch.inner = inst->plan_inner;
+  const Plan p = make_plan(m, n, ch);
   cudaStream_t s = inst->stream;
   msp_stats &st = inst->stats;
   st = msp_stats{};
@@ -752,6 +757,18 @@ const char *msp_last_error(void) { return g_err.c_str(); }
 
 const char *msp_version(void) { return "libmsp 0.1 (sm_103a)"; }
 
+const char *msp_device_name(void) {
+  thread_local std::string name;
+  name.clear();
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+    name = prop.name;
+  else
+    cudaGetLastError();
+  return name.c_str();
+}
+
 int msp_create(const int32_t *A, const int32_t *d, int m, int n, msp_instance **out) {
   if (!out) return fail(MSP_EINVAL, "out must be non-null");
   *out = nullptr;
@@ -820,6 +837,18 @@ int msp_set_option(msp_instance *inst, int option, int64_t value) {
     case MSP_OPT_CLASS_PARTS:
       if (value < 1) return fail(MSP_EINVAL, "class parts must be >= 1");
       inst->parts = value;
+      return MSP_OK;
+    case MSP_OPT_CLASS_BITS:
+      if (value < -1 || value > 23) return fail(MSP_ERANGE, "class bits must lie in [-1, 23]");
+      inst->plan_B = static_cast<int>(value);
+      return MSP_OK;
+    case MSP_OPT_DIGIT_BITS:
+      if (value < -1 || value > 12) return fail(MSP_ERANGE, "digit bits must lie in [-1, 12]");
+      inst->plan_D = static_cast<int>(value);
+      return MSP_OK;
+    case MSP_OPT_INNER_BITS:
+      if (value < -1 || value > 12) return fail(MSP_ERANGE, "inner bits must lie in [-1, 12]");
+      inst->plan_inner = static_cast<int>(value);
       return MSP_OK;
     default:
       return fail(MSP_EINVAL, "unknown option");

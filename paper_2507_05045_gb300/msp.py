@@ -25,8 +25,13 @@ EXPORTED_SYMBOLS = (
     "msp_create", "msp_destroy", "msp_set_stream", "msp_set_memory_budget", "msp_solve_all",
     "msp_get_stats", "msp_free_solutions", "msp_set_profiling", "msp_set_option", "msp_solve_batch", "msp_server_create", "msp_submit",
     "msp_poll", "msp_cancel", "msp_server_destroy", "msp_last_error", "msp_version",
-    "msp_solve_small_noalloc",
+    "msp_solve_small_noalloc", "msp_device_name",
 )
+
+# msp_set_option codes (include/msp.h)
+OPT_EXACT_PATH, OPT_CLASS_PART, OPT_CLASS_PARTS = 1, 2, 3
+OPT_CLASS_BITS, OPT_DIGIT_BITS, OPT_INNER_BITS = 4, 5, 6
+PLAN_KEYS = {"class_bits": OPT_CLASS_BITS, "digit_bits": OPT_DIGIT_BITS, "inner_bits": OPT_INNER_BITS}
 
 STATUS = {0: "MSP_OK", 1: "MSP_PENDING", -1: "MSP_EINVAL", -2: "MSP_ERANGE", -3: "MSP_ENOMEM",
           -4: "MSP_ECUDA", -5: "MSP_ETIMEDOUT", -6: "MSP_EOVERFLOW", -7: "MSP_ECANCELED"}
@@ -113,6 +118,7 @@ def load_library(path: str | None = None):
         lib.msp_solve_small_noalloc.restype = ctypes.c_int
         lib.msp_last_error.restype = ctypes.c_char_p
         lib.msp_version.restype = ctypes.c_char_p
+        lib.msp_device_name.restype = ctypes.c_char_p
         _lib = lib
         return lib
 
@@ -140,7 +146,10 @@ class Instance:
     """One (A, d) instance: ``msp_create`` / ``msp_solve_all`` / ``msp_destroy``."""
 
     def __init__(self, A, d, stream: int | None = None, memory_budget: int = 0, profiling: bool = False,
-                 exact_path: bool = False, class_part: tuple[int, int] | None = None):
+                 exact_path: bool = False, class_part: tuple[int, int] | None = None, plan=None):
+        """``plan``: None (built-in formulas), a dict with any of ``class_bits``,
+        ``digit_bits``, ``inner_bits`` (see MSP_OPT_* in msp.h), or ``"auto"``
+        for the autotuner's cached choice for this device and (m, n), if any."""
         lib = load_library()
         A = np.asarray(A)
         if A.ndim != 2:
@@ -163,8 +172,18 @@ class Instance:
         if exact_path:
             _check(lib.msp_set_option(h, 1, 1))
         if class_part is not None:
-            _check(lib.msp_set_option(h, 3, int(class_part[1])))
-            _check(lib.msp_set_option(h, 2, int(class_part[0])))
+            _check(lib.msp_set_option(h, OPT_CLASS_PARTS, int(class_part[1])))
+            _check(lib.msp_set_option(h, OPT_CLASS_PART, int(class_part[0])))
+        if isinstance(plan, str):
+            if plan != "auto":
+                raise MspError(-1, "plan must be None, a dict or 'auto'")
+            from . import autotune
+            plan = autotune.cached_plan(self.m, self.n)
+        self.plan = dict(plan) if plan else {}
+        for k, v in self.plan.items():
+            if k not in PLAN_KEYS:
+                raise MspError(-1, f"unknown plan key {k!r}")
+            _check(lib.msp_set_option(h, PLAN_KEYS[k], int(v)))
 
     def solve_all(self):
         ptr = ctypes.POINTER(ctypes.c_uint64)()

@@ -293,3 +293,49 @@ def test_class_parts_partition_the_solution_set(msp):
     assert sorted(union) == full
     assert recs == st_full["records_done"] == st_full["records_left"] + st_full["records_right"]
     assert mi.mask_of(x) in full
+
+
+@pytest.mark.parametrize("plan", [
+    {"class_bits": 3, "digit_bits": 2, "inner_bits": 3},
+    {"class_bits": 6, "digit_bits": 4, "inner_bits": 6},
+    {"class_bits": 0, "digit_bits": 0},     # one class, unsplit: exact-path passes
+    {"class_bits": 9, "digit_bits": 0, "inner_bits": 0},
+    {"inner_bits": 12},
+])
+def test_plan_choices_give_the_oracle_solutions(msp, plan):
+    # every plan the autotuner may set splits the same work differently and
+    # must return exactly the golden solution set
+    for e, A, d, x, sols in load_golden("sols_6_50_batch.json")[:4]:
+        with msp.Instance(A, d, plan=plan) as inst:
+            got = inst.solve_all()
+            st = inst.stats()
+        assert got == sols, (plan, e["seed"])
+        if "class_bits" in plan:
+            assert st["class_bits"] == plan["class_bits"]
+        if "digit_bits" in plan:
+            assert st["digit_bits"] == plan["digit_bits"]
+
+
+def test_plan_options_are_validated(msp):
+    A, d, _ = mi.generate(4, 30, 1)
+    for bad in [{"class_bits": 24}, {"digit_bits": 13}, {"inner_bits": -2}]:
+        with pytest.raises(msp.MspError) as e:
+            msp.Instance(A, d, plan=bad)
+        assert e.value.code == -2
+    with pytest.raises(msp.MspError):
+        msp.Instance(A, d, plan={"unknown": 1})
+
+
+def test_autotune_picks_a_cached_plan_with_oracle_solutions(msp, tmp_path, monkeypatch):
+    from paper_2507_05045_gb300 import autotune
+    monkeypatch.setenv(autotune.CACHE_ENV, str(tmp_path / "tune.json"))
+    res = autotune.autotune(6, 50, sample_records=2 ** 24)
+    assert not res["cached"]
+    assert len(res["table"]) >= 2
+    assert res["projected_s"] <= res["default_projected_s"]
+    again = autotune.autotune(6, 50)
+    assert again["cached"] and again["plan"] == res["plan"]
+    e, A, d, x, sols = load_golden("sols_6_50_batch.json")[1]
+    with msp.Instance(A, d, plan="auto") as inst:
+        assert inst.plan == res["plan"]
+        assert inst.solve_all() == sols
