@@ -88,6 +88,8 @@ typedef struct {
   uint64_t classes_total;     /* residue classes of the instance (2^class_bits) */
   uint64_t classes_done;      /* classes this solve enumerated                */
   uint64_t records_done;      /* half-pair records (both sides) it generated   */
+  int path;                   /* pass that solved it: 0 streaming / exact, 1 direct */
+  int direct_fallback;        /* 1: the direct pass handed the solve to the others */
   /* Filled only when profiling is on (msp_set_profiling): per kernel kind
    * (MSP_K_* below) the summed CUDA-event time, the launches, and the
    * algorithmic device-memory bytes (records written / read x 8 bytes). */
@@ -108,7 +110,8 @@ enum {
   MSP_K_JOIN_BIG = 7,  /* oversize partitions                        */
   MSP_K_RECOVER = 8,   /* quarter elements behind matched keys       */
   MSP_K_VERIFY = 9,    /* exact all-row check                        */
-  MSP_K_OTHER = 10
+  MSP_K_OTHER = 10,
+  MSP_K_DIRECT = 11    /* direct pass: class joins in shared memory   */
 };
 
 /* Validate and copy (A row-major m x n, d length m); upload to the device.
@@ -126,10 +129,11 @@ MSP_API int msp_set_stream(msp_instance *inst, void *cuda_stream);
 MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
 
 /* Instance options (msp_set_option):
- *   MSP_OPT_EXACT_PATH  1 = skip the streaming pass and run every residue
- *                       pass on the exact two-phase path (count, then
- *                       scatter); 0 = default (streaming, exact re-run of
- *                       any pass whose partitions overflow). */
+ *   MSP_OPT_EXACT_PATH  1 = skip the direct and streaming passes and run
+ *                       every residue pass on the exact two-phase path
+ *                       (count, then scatter); 0 = default (direct pass when
+ *                       the instance fits it, else streaming with an exact
+ *                       re-run of any pass whose partitions overflow). */
 /*   MSP_OPT_CLASS_PART, MSP_OPT_CLASS_PARTS  enumerate only the residue
  *                       classes [k*M/P, (k+1)*M/P) of the M classes, with
  *                       k = PART and P = PARTS (default 0 of 1: all).  The
@@ -150,13 +154,29 @@ MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
  *                        For these three, -1 (the default) restores the
  *                        built-in formula; any choice gives the same solutions.
  *                        They are what the package's autotuner sets per (m, n). */
+/*   MSP_OPT_DIRECT       the direct pass (default for every instance it
+ *                        fits: halves of at most 40 columns): the columns of
+ *                        each half are split into an outer quarter of at most
+ *                        2^10 subsets and an inner quarter bucketed into
+ *                        residue classes of about 16 subsets, so a thread
+ *                        block joins a whole class (about 2^13 records per
+ *                        side) in shared memory and no record is written to
+ *                        device memory.  1 = use it whenever the instance fits
+ *                        (the three streaming-pass options above are then
+ *                        ignored), 0 = never, -1 (default) = use it unless one
+ *                        of the three streaming-pass options is set.
+ *   MSP_OPT_TABLE_BITS   shared hash table of the direct pass: 2^value slots,
+ *                        value in [12, 15]; -1 = 14.
+ *                        Either choice gives the same solutions. */
 enum {
   MSP_OPT_EXACT_PATH = 1,
   MSP_OPT_CLASS_PART = 2,
   MSP_OPT_CLASS_PARTS = 3,
   MSP_OPT_CLASS_BITS = 4,
   MSP_OPT_DIGIT_BITS = 5,
-  MSP_OPT_INNER_BITS = 6
+  MSP_OPT_INNER_BITS = 6,
+  MSP_OPT_DIRECT = 7,
+  MSP_OPT_TABLE_BITS = 8
 };
 MSP_API int msp_set_option(msp_instance *inst, int option, int64_t value);
 

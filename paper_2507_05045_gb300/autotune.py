@@ -1,12 +1,15 @@
 """Per-(m, n) plan autotuner.
 
-A plan fixes the residue modulus 2^B (class bits), the radix digit width D of
-the streaming pass (partitions of about |L| / 2^(B + D) records) and the
-uneven quarter split (inner bits: an inner residue bucket holds about
-2^inner elements, the run one outer element expands to in the scatter).  The
-library picks them by formula; this module times candidate plans around that
-choice on a seeded sample of residue classes of an instance of the shape and
-keeps the one with the smallest projected time to all solutions.  Results are
+A plan picks the enumeration path and its tile sizes.  The direct pass
+(classes joined in shared memory) has one knob, the shared hash table of
+2^table_bits slots.  The streaming pass has three: the residue modulus 2^B
+(class bits), the radix digit width D (partitions of about |L| / 2^(B + D)
+records) and the uneven quarter split (inner bits: an inner residue bucket
+holds about 2^inner elements, the run one outer element expands to in the
+scatter).  The library picks them by formula; this module times candidate
+plans of both paths on a seeded sample of residue classes of an instance of
+the shape and keeps the one with the smallest projected time to all
+solutions.  Results are
 cached in a JSON file keyed by the device name and (m, n); ``Instance(...,
 plan="auto")`` reads the cache.
 
@@ -29,8 +32,10 @@ _lock = threading.Lock()
 
 # kernels whose time grows with the number of classes solved (the rest build
 # the quarter lists once per solve)
-_PER_CLASS = ("gen_count", "offsets", "gen_scatter", "join", "join_big", "other")
-_PER_SOLVE = ("gray", "bucket", "c1", "recover", "verify")
+_PER_CLASS = ("gen_count", "offsets", "gen_scatter", "join", "join_big", "other", "direct", "recover",
+              "verify")
+_PER_SOLVE = ("gray", "bucket", "c1")
+STREAM_KEYS = ("class_bits", "digit_bits", "inner_bits")
 
 
 def cache_path() -> str:
@@ -81,14 +86,17 @@ def record_plan(m: int, n: int, plan: dict, info: dict | None = None, path: str 
         _store(path, data)
 
 
-def candidates(base: dict, lg: int) -> list[dict]:
-    """Plans around the formula's choice ``base`` (class_bits B0, digit_bits
-    D0) for sides of 2^lg records: B0 - 1 .. B0 + 1 classes, partitions of
-    about 2^12 or 2^11 records (the streaming join holds at most 4608), inner
-    buckets of about 2^3 .. 2^5 elements.  The formula's own plan comes
-    first."""
+def candidates(base: dict, lg: int, direct: bool = True) -> list[dict]:
+    """Candidate plans for sides of 2^lg records.  With ``direct`` (the
+    instance fits the direct pass, the formula's default) the direct pass
+    with tables of 2^14, 2^13 and 2^15 slots comes first.  Then the streaming
+    pass around the formula's choice ``base`` (class_bits B0, digit_bits D0):
+    B0 - 1 .. B0 + 1 classes, partitions of about 2^12 or 2^11 records (the
+    streaming join holds at most 4608), inner buckets of about 2^3 .. 2^5
+    elements, the formula's own streaming plan first."""
     B0, D0 = base["class_bits"], base["digit_bits"]
-    out = [dict(base)]
+    out = [{"direct": 1, "table_bits": tb} for tb in (14, 13, 15)] if direct else []
+    out.append(dict(base, direct=0))
     for B in (B0 - 1, B0, B0 + 1):
         if B < 0 or B > 23:
             continue
@@ -97,7 +105,7 @@ def candidates(base: dict, lg: int) -> list[dict]:
             if D < 0 or D > 12:
                 continue
             for inner in (3, 4, 5):
-                c = {"class_bits": B, "digit_bits": D, "inner_bits": inner}
+                c = {"class_bits": B, "digit_bits": D, "inner_bits": inner, "direct": 0}
                 if c not in out:
                     out.append(c)
     return out
@@ -122,13 +130,14 @@ def measure(A, d, plan: dict | None, parts: int) -> dict:
         st = inst.stats()
     k = st["kernels"]
     per_class = sum(k[x]["ms"] for x in _PER_CLASS if x in k)
+    path = st["path"]
     per_solve = sum(k[x]["ms"] for x in _PER_SOLVE if x in k)
     total = st["records_left"] + st["records_right"]
     done = max(1, st["records_done"])
     proj_ms = per_class * total / done + per_solve
     return {"projected_s": proj_ms / 1e3, "sample_s": wall, "records_done": st["records_done"],
             "class_bits": st["class_bits"], "digit_bits": st["digit_bits"], "quarter": st["quarter"],
-            "redone": st["fast_passes_redone"]}
+            "redone": st["fast_passes_redone"] + st["direct_fallback"], "path": path}
 
 
 def _parts_for(A, d, plan, sample_records: float) -> int:
@@ -158,14 +167,17 @@ def autotune(m: int, n: int, A=None, d=None, sample_records: float = 2 ** 33, se
     A = np.asarray(A, dtype=np.int32)
     d = np.asarray(d, dtype=np.int32).reshape(-1)
     with msp.Instance(A, d, class_part=(0, 1 << 30)) as inst:
-        inst.solve_all()  # no class: the formula's plan in the stats
+        inst.solve_all()  # no class: the formula's default path in the stats
+        direct_ok = inst.stats()["path"] == "direct"
+    with msp.Instance(A, d, class_part=(0, 1 << 30), plan={"direct": 0}) as inst:
+        inst.solve_all()  # the formula's streaming plan
         st = inst.stats()
     q = st["quarter"]
     lg = max(q[0] + q[2], q[1] + q[3])
     base = {"class_bits": st["class_bits"], "digit_bits": st["digit_bits"], "inner_bits": 4}
     table = []
     best = None
-    for plan in candidates(base, lg):
+    for plan in candidates(base, lg, direct_ok):
         r = measure(A, d, plan, _parts_for(A, d, plan, sample_records))
         r["plan"] = plan
         table.append(r)

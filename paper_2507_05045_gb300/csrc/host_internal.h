@@ -24,6 +24,8 @@ struct msp_instance {
   bool force_exact = false;
   int64_t part = 0, parts = 1;  // residue-class subset [part*M/parts, (part+1)*M/parts)
   int plan_B = -1, plan_D = -1, plan_inner = -1;  // plan overrides (-1 = formula)
+  int direct = -1;      // direct pass: -1 auto, 0 never, 1 whenever the instance fits it
+  int table_bits = -1;  // direct pass shared-table bits (-1 = default)
 };
 
 namespace msp {
@@ -61,4 +63,29 @@ int solve_batch_impl(const int32_t *const *A, const int32_t *const *d, int m, in
                      std::vector<std::vector<uint64_t>> &raw, cudaStream_t s, size_t budget);
 // Device bytes of the quarter lists plus one residue pass (capped at cap).
 size_t footprint_estimate(int m, int n, size_t cap);
+
+// Direct pass (direct.cu): the columns of each half are split into an outer
+// quarter of at most 2^10 subsets and an inner quarter bucketed into 2^B
+// residue classes of about 16 subsets, so that one block joins a class
+// (about 2^13 records per side) in shared memory.
+struct DirectPlan {
+  bool ok;            // the instance fits the direct pass
+  int m, n, W;
+  int cols[2];        // columns of L (the first ceil(n/2)) and R
+  int qo[2], qi[2];   // outer and inner quarter columns per side
+  int col_o[2], col_i[2];
+  int B, t;           // residue classes 2^B over rows 1..t
+  int TB;             // shared table of 2^TB slots
+};
+DirectPlan make_direct_plan(int m, int n, int table_bits);
+// Device bytes of a direct solve.
+size_t direct_footprint(const DirectPlan &d);
+constexpr int kDirectFallback = 2;            // solve_direct: use another path
+constexpr uint64_t kDirectMatchCap = 1u << 23;  // matched (class, key) pairs held
+struct Prof;
+int solve_direct(msp_instance *inst, const DirectPlan &dp, const Plan &kp, size_t budget, Prof &prof,
+                 std::vector<uint64_t> &res);
+// Device memory a solve may use: the instance budget, else 85% of what is
+// free (counting the stream-ordered pool's unused memory as free).
+size_t solve_budget(const msp_instance *inst, size_t already_held);
 }  // namespace msp

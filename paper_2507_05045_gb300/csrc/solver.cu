@@ -124,6 +124,24 @@ uint32_t class_of(const Plan &p, const int64_t *v) {
   for (int i = 0; i < p.t; ++i) c += p.c_row[i] * static_cast<uint32_t>(v[i]);
   return p.B ? (c & ((1u << p.B) - 1u)) : 0u;
 }
+
+size_t solve_budget(const msp_instance *inst, size_t already_held) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return inst->budget;
+  }
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, inst->device) == cudaSuccess) {
+    uint64_t reserved = 0, used = 0;
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    if (reserved > used) free_b += reserved - used;
+  }
+  const double avail = (double)free_b + (double)already_held;
+  size_t budget = inst->budget ? inst->budget : static_cast<size_t>(0.85 * avail);
+  return std::min(budget, static_cast<size_t>(0.95 * avail));
+}
 }  // namespace msp
 
 namespace {
@@ -158,6 +176,34 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     for (int j = 0; j < n; ++j) rowsum[i] += inst->A[(size_t)i * n + j];
   for (int i = 0; i < m; ++i)
     if (inst->d[i] > rowsum[i]) return MSP_OK;
+
+  // ---- the direct pass (direct.cu) for every instance it fits ----
+  {
+    const bool stream_plan = inst->plan_B >= 0 || inst->plan_D >= 0 || inst->plan_inner >= 0;
+    const bool want = !inst->force_exact && (inst->direct == 1 || (inst->direct < 0 && !stream_plan));
+    const DirectPlan dp = make_direct_plan(m, n, inst->table_bits);
+    if (want && dp.ok) {
+      const msp_stats st0 = st;
+      Prof dprof;
+      dprof.on = inst->profiling;
+      dprof.s = s;
+      dprof.st = &st;
+      std::vector<uint64_t> raw;
+      const int rc = solve_direct(inst, dp, p, solve_budget(inst, 0), dprof, raw);
+      if (rc == MSP_OK) {
+        st.path = 1;
+        res->masks = std::move(raw);
+        return MSP_OK;
+      }
+      if (rc != kDirectFallback) return rc;
+      // the streaming and exact passes solve it; the direct attempt's
+      // launches stay counted
+      const uint64_t launches = st.kernel_launches;
+      st = st0;
+      st.kernel_launches = launches;
+      st.direct_fallback = 1;
+    }
+  }
 
   // ---- S0: packed columns, key and class of every column, constants ----
   InstanceConst ic{};
@@ -300,20 +346,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
   }
   // memory budget: free device memory, plus what the stream-ordered pool
   // holds unused from earlier solves, plus this solve's own allocations
-  size_t free_b = 0, total_b = 0;
-  CK(cudaMemGetInfo(&free_b, &total_b));
-  {
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, inst->device) == cudaSuccess) {
-      uint64_t reserved = 0, used = 0;
-      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
-      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
-      if (reserved > used) free_b += reserved - used;
-    }
-  }
-  const double avail = (double)free_b + (double)da.bytes;
-  size_t budget = inst->budget ? inst->budget : static_cast<size_t>(0.85 * avail);
-  budget = std::min(budget, static_cast<size_t>(0.95 * avail));
+  const size_t budget = solve_budget(inst, da.bytes);
   const size_t fixed_reserve = (size_t)64 << 20;  // matches and small per-pass tables
 
   uint64_t *match_key;
@@ -734,6 +767,14 @@ int solve_instance(msp_instance *inst, uint64_t **masks, size_t *count, int *wor
 // Device bytes a solve of an (m, n) instance needs for its quarter lists and
 // one residue pass of at least one class, capped at `cap` (0 = no cap).
 size_t footprint_estimate(int m, int n, size_t cap) {
+  {
+    // the direct pass, when the instance fits it and its lists fit the cap
+    const DirectPlan dp = make_direct_plan(m, n, -1);
+    if (dp.ok) {
+      const size_t dneed = direct_footprint(dp);
+      if (!cap || dneed <= cap) return dneed;
+    }
+  }
   const Plan p = make_plan(m, n);
   double fixed = 0;
   // quarter lists (packed rows, key, class, row 1) and their class buckets
@@ -849,6 +890,14 @@ int msp_set_option(msp_instance *inst, int option, int64_t value) {
     case MSP_OPT_INNER_BITS:
       if (value < -1 || value > 12) return fail(MSP_ERANGE, "inner bits must lie in [-1, 12]");
       inst->plan_inner = static_cast<int>(value);
+      return MSP_OK;
+    case MSP_OPT_DIRECT:
+      if (value < -1 || value > 1) return fail(MSP_ERANGE, "direct must be -1, 0 or 1");
+      inst->direct = static_cast<int>(value);
+      return MSP_OK;
+    case MSP_OPT_TABLE_BITS:
+      if (value != -1 && (value < 12 || value > 15)) return fail(MSP_ERANGE, "table bits must be -1 or lie in [12, 15]");
+      inst->table_bits = static_cast<int>(value);
       return MSP_OK;
     default:
       return fail(MSP_EINVAL, "unknown option");

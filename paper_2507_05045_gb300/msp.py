@@ -31,7 +31,9 @@ EXPORTED_SYMBOLS = (
 # msp_set_option codes (include/msp.h)
 OPT_EXACT_PATH, OPT_CLASS_PART, OPT_CLASS_PARTS = 1, 2, 3
 OPT_CLASS_BITS, OPT_DIGIT_BITS, OPT_INNER_BITS = 4, 5, 6
-PLAN_KEYS = {"class_bits": OPT_CLASS_BITS, "digit_bits": OPT_DIGIT_BITS, "inner_bits": OPT_INNER_BITS}
+OPT_DIRECT, OPT_TABLE_BITS = 7, 8
+PLAN_KEYS = {"class_bits": OPT_CLASS_BITS, "digit_bits": OPT_DIGIT_BITS, "inner_bits": OPT_INNER_BITS,
+             "direct": OPT_DIRECT, "table_bits": OPT_TABLE_BITS}
 
 STATUS = {0: "MSP_OK", 1: "MSP_PENDING", -1: "MSP_EINVAL", -2: "MSP_ERANGE", -3: "MSP_ENOMEM",
           -4: "MSP_ECUDA", -5: "MSP_ETIMEDOUT", -6: "MSP_EOVERFLOW", -7: "MSP_ECANCELED"}
@@ -54,16 +56,18 @@ class Stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
                 ("fast_passes_redone", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
                 ("classes_total", ctypes.c_uint64), ("classes_done", ctypes.c_uint64),
-                ("records_done", ctypes.c_uint64),
+                ("records_done", ctypes.c_uint64), ("path", ctypes.c_int), ("direct_fallback", ctypes.c_int),
                 ("kernel_ms", ctypes.c_double * 12), ("kernel_count", ctypes.c_uint64 * 12),
                 ("kernel_bytes", ctypes.c_uint64 * 12)]
 
     KINDS = ("gray", "bucket", "c1", "gen_count", "offsets", "gen_scatter", "join", "join_big",
-             "recover", "verify", "other")
+             "recover", "verify", "other", "direct")
+    PATHS = ("streaming", "direct")
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["quarter"] = list(self.quarter)
+        d["path"] = self.PATHS[self.path] if 0 <= self.path < len(self.PATHS) else self.path
         d["row1_candidates"] = int(self.row1_candidates_lo) | (int(self.row1_candidates_hi) << 64)
         d["kernels"] = {k: {"ms": self.kernel_ms[i], "launches": int(self.kernel_count[i]),
                             "bytes": int(self.kernel_bytes[i])}
@@ -148,8 +152,10 @@ class Instance:
     def __init__(self, A, d, stream: int | None = None, memory_budget: int = 0, profiling: bool = False,
                  exact_path: bool = False, class_part: tuple[int, int] | None = None, plan=None):
         """``plan``: None (built-in formulas), a dict with any of ``class_bits``,
-        ``digit_bits``, ``inner_bits`` (see MSP_OPT_* in msp.h), or ``"auto"``
-        for the autotuner's cached choice for this device and (m, n), if any."""
+        ``digit_bits``, ``inner_bits`` (streaming pass), ``direct`` (-1, 0, 1)
+        and ``table_bits`` (direct pass; see MSP_OPT_* in msp.h), or
+        ``"auto"`` for the autotuner's cached choice for this device and
+        (m, n), if any."""
         lib = load_library()
         A = np.asarray(A)
         if A.ndim != 2:

@@ -9,21 +9,28 @@ from paper_2507_05045_gb300 import autotune, msp
 def test_candidates_start_with_the_formula_plan_and_are_distinct():
     base = {"class_bits": 19, "digit_bits": 9, "inner_bits": 4}
     cands = autotune.candidates(base, 40)
-    assert cands[0] == base
+    # the direct pass (the formula's default) with its table sizes first
+    assert cands[0] == {"direct": 1, "table_bits": 14}
+    assert [c for c in cands if c["direct"] == 1] == cands[:3]
+    assert {c["table_bits"] for c in cands[:3]} == {13, 14, 15}
+    assert cands[3] == dict(base, direct=0)
     keys = [tuple(sorted(c.items())) for c in cands]
     assert len(keys) == len(set(keys))
-    for c in cands:
-        assert set(c) == set(msp.PLAN_KEYS)
+    for c in cands[3:]:
+        assert set(c) == set(autotune.STREAM_KEYS) | {"direct"} and c["direct"] == 0
+        assert set(c) <= set(msp.PLAN_KEYS)
         assert 0 <= c["class_bits"] <= 23 and 0 <= c["digit_bits"] <= 12
         assert abs(c["class_bits"] - 19) <= 1
         # partitions of 2^11 .. 2^12 records: inside the streaming join's capacity
-        if c is not cands[0]:
+        if c is not cands[3]:
             assert 40 - c["class_bits"] - c["digit_bits"] in (11, 12)
+    # an instance the direct pass does not fit gets streaming plans only
+    assert all(c["direct"] == 0 for c in autotune.candidates(base, 45, direct=False))
 
 
 def test_candidates_respect_the_bounds():
     for lg, B0, D0 in [(15, 0, 3), (50, 23, 12), (1, 0, 0)]:
-        for c in autotune.candidates({"class_bits": B0, "digit_bits": D0, "inner_bits": 4}, lg):
+        for c in autotune.candidates({"class_bits": B0, "digit_bits": D0, "inner_bits": 4}, lg, False):
             assert 0 <= c["class_bits"] <= 23
             assert 0 <= c["digit_bits"] <= 12
 

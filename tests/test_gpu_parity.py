@@ -17,6 +17,19 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
+# the two enumeration paths of a solve: the direct pass (classes joined in
+# shared memory) and the streaming / exact residue passes
+PATHS = [pytest.param({"direct": 1}, id="direct"), pytest.param({"direct": 0}, id="streaming")]
+
+
+def solve(msp, A, d, plan, expect_path=True):
+    with msp.Instance(A, d, plan=plan) as inst:
+        got = inst.solve_all()
+        st = inst.stats()
+    if expect_path and plan.get("direct") == 0:
+        assert st["path"] == "streaming"
+    return got, st
+
 
 @pytest.fixture(scope="module")
 def msp():
@@ -42,56 +55,62 @@ def load_golden(name):
     return out
 
 
-def test_hand_instances(msp):
+@pytest.mark.parametrize("plan", PATHS)
+def test_hand_instances(msp, plan):
     g = json.load(open(os.path.join(GOLDEN, "hand_instances.json")))
     for inst in g["instances"]:
-        got = [s[0] for s in msp.solve_all(np.array(inst["A"]), np.array(inst["d"]))]
-        assert got == inst["solutions"], inst["name"]
+        got, _ = solve(msp, np.array(inst["A"]), np.array(inst["d"]), plan)
+        assert [s[0] for s in got] == inst["solutions"], inst["name"]
 
 
+@pytest.mark.parametrize("plan", PATHS)
 @pytest.mark.parametrize("seed", range(40))
-def test_random_small_vs_brute(msp, seed):
+def test_random_small_vs_brute(msp, seed, plan):
     rng = np.random.default_rng(seed)
     m = int(rng.integers(1, 11))
     n = int(rng.integers(1, 23))
     K = int(rng.choice([2, 3, 5, 20, 100]))
     A, d, _ = mi.generate(m, n, 5000 + seed, K=K, planted=bool(seed % 2), h=n // 2)
-    assert msp.solve_all(A, d) == oracle.brute(A, d)
+    got, st = solve(msp, A, d, plan)
+    assert got == oracle.brute(A, d)
 
 
+@pytest.mark.parametrize("plan", PATHS)
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 9, 13])
-def test_tiny_n_every_quarter_shape(msp, n):
+def test_tiny_n_every_quarter_shape(msp, n, plan):
     for seed in range(3):
         A, d, _ = mi.generate(2, n, 90 + seed, K=3, planted=True, h=n // 2)
-        assert msp.solve_all(A, d) == oracle.brute(A, d)
+        assert solve(msp, A, d, plan)[0] == oracle.brute(A, d)
 
 
-def test_degenerate_inputs(msp):
+@pytest.mark.parametrize("plan", PATHS)
+def test_degenerate_inputs(msp, plan):
     # all-zero matrix: every vector solves d = 0, none solves d != 0
     A = np.zeros((3, 12), np.int32)
-    assert [s[0] for s in msp.solve_all(A, [0, 0, 0])] == list(range(1 << 12))
-    assert msp.solve_all(A, [0, 1, 0]) == []
+    assert [s[0] for s in solve(msp, A, [0, 0, 0], plan)[0]] == list(range(1 << 12))
+    assert solve(msp, A, [0, 1, 0], plan, False)[0] == []
     # right-hand side above a row sum
     A, d, _ = mi.generate(3, 16, 3)
     d2 = d.copy()
     d2[1] = A[1].sum() + 1
-    assert msp.solve_all(A, d2) == []
+    assert solve(msp, A, d2, plan, False)[0] == []
     # d = 0 with positive entries: x = 0 only
     A = np.arange(1, 21, dtype=np.int32).reshape(2, 10)
-    assert msp.solve_all(A, [0, 0]) == [(0,)]
+    assert solve(msp, A, [0, 0], plan)[0] == [(0,)]
     # zero columns and duplicate rows
     A, d, _ = mi.generate(3, 18, 4, K=4, planted=True, h=9)
     A2 = np.hstack([A, np.zeros((3, 2), np.int32)])
     A2 = np.vstack([A2, A2[0:1]])
     d2 = np.concatenate([d, d[0:1]])
-    assert msp.solve_all(A2, d2) == oracle.brute(A2, d2)
+    assert solve(msp, A2, d2, plan)[0] == oracle.brute(A2, d2)
 
 
+@pytest.mark.parametrize("plan", PATHS)
 @pytest.mark.parametrize("seed", range(6))
-def test_small_K_long_equal_key_runs(msp, seed):
+def test_small_K_long_equal_key_runs(msp, seed, plan):
     # K = 2: many subsets share one vector, so keys repeat in long runs
     A, d, _ = mi.generate(2, 22, 6000 + seed, K=2, planted=True, h=11)
-    assert msp.solve_all(A, d) == oracle.brute(A, d)
+    assert solve(msp, A, d, plan)[0] == oracle.brute(A, d)
 
 
 def test_config_4_30(msp):
@@ -102,18 +121,21 @@ def test_config_4_30(msp):
             assert mi.mask_of(x) in got
 
 
+@pytest.mark.parametrize("plan", PATHS)
 @pytest.mark.parametrize("seed", range(4))
-def test_5_40_vs_mitm(msp, seed):
+def test_5_40_vs_mitm(msp, seed, plan):
     A, d, _ = mi.generate(5, 40, 7000 + seed, planted=bool(seed % 2), h=20)
-    assert msp.solve_all(A, d) == oracle.mitm(A, d)
+    got, st = solve(msp, A, d, plan)
+    assert got == oracle.mitm(A, d)
+    if plan["direct"]:
+        assert st["path"] == "direct"
 
 
-def test_row1_candidate_count_matches_counting_dp(msp):
+@pytest.mark.parametrize("plan", PATHS)
+def test_row1_candidate_count_matches_counting_dp(msp, plan):
     for (m, n, seed) in [(4, 30, 1), (5, 40, 2), (6, 50, 3), (3, 22, 4)]:
         A, d, _ = mi.generate(m, n, seed)
-        with msp.Instance(A, d) as inst:
-            inst.solve_all()
-            st = inst.stats()
+        _, st = solve(msp, A, d, plan)
         assert st["row1_candidates"] == oracle.row1_candidates(A, d)
 
 
@@ -126,29 +148,34 @@ def test_config_6_50_batch(msp):
             assert mi.mask_of(x) in g
 
 
-def test_config_6_50_single(msp):
+@pytest.mark.parametrize("plan", PATHS)
+def test_config_6_50_single(msp, plan):
     for e, A, d, x, sols in load_golden("sols_6_50_batch.json")[:8]:
-        assert msp.solve_all(A, d) == sols
+        got, st = solve(msp, A, d, plan)
+        assert got == sols
+        if plan["direct"]:
+            assert st["path"] == "direct"
 
 
 def test_many_passes_same_result(msp):
     # a small budget forces many residue passes: the set must not change
     e, A, d, x, sols = load_golden("sols_6_50_batch.json")[40]
-    with msp.Instance(A, d, memory_budget=400 << 20) as inst:
+    with msp.Instance(A, d, memory_budget=400 << 20, plan={"direct": 0}) as inst:
         got = inst.solve_all()
         st = inst.stats()
     assert got == sols
     assert st["passes"] >= 1
 
 
+@pytest.mark.parametrize("plan", PATHS)
 @pytest.mark.parametrize("name", ["sols_7_60.json", "sols_7_60_planted.json"])
-def test_config_7_60(msp, name):
+def test_config_7_60(msp, name, plan):
     for e, A, d, x, sols in load_golden(name):
-        with msp.Instance(A, d) as inst:
-            got = inst.solve_all()
-            st = inst.stats()
+        got, st = solve(msp, A, d, plan)
         assert got == sols
         assert st["row1_candidates"] == oracle.row1_candidates(A, d)
+        if plan["direct"]:
+            assert st["path"] == "direct"
 
 
 def _check_solutions_exact(A, d, sols):
@@ -182,11 +209,10 @@ def _subcube_parity(msp_sols, A, d, fixed_cols, fixed_vals):
     assert sorted(got) == sorted(lifted)
 
 
-def test_config_8_70_planted_properties_and_subcube(msp):
+@pytest.mark.parametrize("plan", PATHS)
+def test_config_8_70_planted_properties_and_subcube(msp, plan):
     A, d, x = mi.generate(8, 70, 8, planted=True, h=35)
-    with msp.Instance(A, d) as inst:
-        sols = inst.solve_all()
-        st = inst.stats()
+    sols, st = solve(msp, A, d, plan)
     assert mi.mask_of(x) in sols
     _check_solutions_exact(A, d, sols)
     assert st["row1_candidates"] == oracle.row1_candidates(A, d)
@@ -202,6 +228,7 @@ def test_config_9_80_planted_properties_and_subcube(msp):
     with msp.Instance(A, d) as inst:
         sols = inst.solve_all()
         st = inst.stats()
+    assert st["path"] == "direct"
     assert mi.mask_of(x) in sols
     _check_solutions_exact(A, d, sols)
     assert st["row1_candidates"] == oracle.row1_candidates(A, d)
@@ -255,8 +282,8 @@ def test_exact_path_matches_streaming_path(msp, seed):
     want = oracle.brute(A, d) if n <= 22 else oracle.mitm(A, d)
     with msp.Instance(A, d, exact_path=True) as inst:
         assert inst.solve_all() == want
-    with msp.Instance(A, d) as inst:
-        assert inst.solve_all() == want
+    assert solve(msp, A, d, {"direct": 0})[0] == want
+    assert solve(msp, A, d, {"direct": 1})[0] == want
 
 
 def test_degenerate_instance_falls_back_to_exact_passes(msp):
@@ -266,24 +293,24 @@ def test_degenerate_instance_falls_back_to_exact_passes(msp):
     A = A.copy()
     A[:, :8] = 0
     d = (A.astype(np.int64) @ x.astype(np.int64)).astype(np.int32)
-    with msp.Instance(A, d) as inst:
-        got = inst.solve_all()
-        st = inst.stats()
-    assert got == oracle.mitm(A, d)
+    want = oracle.mitm(A, d)
+    got, st = solve(msp, A, d, {"direct": 0})
+    assert got == want
     assert len(got) >= 256
     assert st["fast_passes_redone"] >= 1
+    # the direct pass holds each repeated key once in its table
+    assert solve(msp, A, d, {"direct": 1})[0] == want
 
 
-def test_class_parts_partition_the_solution_set(msp):
+@pytest.mark.parametrize("plan", PATHS)
+def test_class_parts_partition_the_solution_set(msp, plan):
     # the solutions of the residue-class parts are disjoint and their union
     # is the full set; records_done adds up to all records
     A, d, x = mi.generate(6, 50, 4321, K=20, planted=True, h=25)
-    with msp.Instance(A, d) as inst:
-        full = inst.solve_all()
-        st_full = inst.stats()
+    full, st_full = solve(msp, A, d, plan)
     parts, union, recs = 4, [], 0
     for k in range(parts):
-        with msp.Instance(A, d, class_part=(k, parts)) as inst:
+        with msp.Instance(A, d, class_part=(k, parts), plan=plan) as inst:
             got = inst.solve_all()
             st = inst.stats()
         assert set(got).isdisjoint(union)
@@ -316,9 +343,37 @@ def test_plan_choices_give_the_oracle_solutions(msp, plan):
             assert st["digit_bits"] == plan["digit_bits"]
 
 
+@pytest.mark.parametrize("tb", [12, 13, 15])
+def test_direct_table_sizes_and_chunked_classes(msp, tb):
+    # a 2^12-slot table holds 3072 left keys: the 2^13-record classes of
+    # (6,50) are joined in three table fills, each probed by every right key
+    for e, A, d, x, sols in load_golden("sols_6_50_batch.json")[:6]:
+        got, st = solve(msp, A, d, {"direct": 1, "table_bits": tb})
+        assert got == sols, (tb, e["seed"])
+        assert st["path"] == "direct"
+    for e, A, d, x, sols in load_golden("sols_7_60_planted.json"):
+        assert solve(msp, A, d, {"direct": 1, "table_bits": tb})[0] == sols
+
+
+def test_direct_pass_on_skewed_classes(msp):
+    # K = 3 and zero columns: few distinct row vectors, classes of very
+    # unequal size and long runs of equal keys; both paths give the oracle set
+    A, _, x = mi.generate(5, 30, 31, K=3, planted=True, h=15)
+    A = A.copy()
+    A[:, 3:6] = 0
+    d = (A.astype(np.int64) @ x.astype(np.int64)).astype(np.int32)
+    want = oracle.mitm(A, d)
+    assert len(want) > 1000
+    for tb in (12, 14):
+        got, st = solve(msp, A, d, {"direct": 1, "table_bits": tb})
+        assert got == want
+    assert solve(msp, A, d, {"direct": 0})[0] == want
+
+
 def test_plan_options_are_validated(msp):
     A, d, _ = mi.generate(4, 30, 1)
-    for bad in [{"class_bits": 24}, {"digit_bits": 13}, {"inner_bits": -2}]:
+    for bad in [{"class_bits": 24}, {"digit_bits": 13}, {"inner_bits": -2}, {"table_bits": 16},
+                {"table_bits": 11}, {"direct": 2}]:
         with pytest.raises(msp.MspError) as e:
             msp.Instance(A, d, plan=bad)
         assert e.value.code == -2
