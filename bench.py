@@ -58,8 +58,10 @@ def parse():
                          "instances in one batched call vs one at a time; serving: the mixed Poisson "
                          "request stream through the server vs sequential solving; 10_90_part: one "
                          "seeded 1/64 of the residue classes of a (10,90) instance; profile_part: "
-                         "the small case the ncu captures use (the (9,80) instance of the default "
-                         "workload over 1/4096 of its residue classes, 1500 MB budget, one solve)")
+                         "the case the ncu captures use (the (9,80) instance of the default "
+                         "workload over 1/4096 of its residue classes, one solve)")
+    ap.add_argument("--path", type=int, default=1, choices=[0, 1],
+                    help="profile_part: 1 = direct pass, 0 = streaming pass")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--rate-factor", type=float, default=0.8)
     return ap.parse_args()
@@ -181,6 +183,17 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
+def l2_note(st):
+    """How a step's device-memory working set compares with the 129 MB L2."""
+    if st.get("path") == "direct":
+        q = st["quarter"]
+        gb = 8.0 * ((1 << q[2]) + (1 << q[3])) / 1e9
+        return (f"inputs larger than L2: the direct pass reads bucketed inner quarter lists of {gb:.1f} GB "
+                f"(32-bit keys plus subset masks) every step; no per-record buffer")
+    return ("inputs larger than L2: every step streams ~16 B per half-pair record through HBM pass "
+            "buffers of tens of GB")
+
+
 def traffic_per_launch(kernel, alg_bytes_per_launch):
     """DRAM bytes per launch from the committed ncu capture, scaled by the
     algorithmic bytes of a launch; None when the kernel source changed since."""
@@ -293,8 +306,7 @@ def native(args, world, rank, local, pg):
         "config": {"workload": f"({args.m},{args.n}) plain instance, exhaustive (all solutions)",
                    "m": args.m, "n": args.n, "seed": SEED, "a_range": "[0,99]",
                    "rhs": "d_i = floor(row sum / 2)", "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2: every step streams ~16 B per half-pair record "
-                         "through HBM pass buffers of tens of GB"},
+                   "l2": l2_note(st0)},
         "time_to_all_solutions_s": ms_max / 1000.0,
         "row1_candidates_per_rank": cand,
         "solutions": len(sols) if sols is not None else None,
@@ -367,6 +379,13 @@ def bench_batch(args):
         rs = [msp.solve_all(A, d) for A, d in pairs]
     ts = (time.perf_counter() - t0) / args.steps
     assert rb == rs
+    # the streaming pass's batch (one scatter and one join launch per pass)
+    msp.solve_batch(pairs, path=0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rst = msp.solve_batch(pairs, path=0)
+    tst = (time.perf_counter() - t0) / args.steps
+    assert rst == rb
     h2d = sum(A.nbytes + d.nbytes for A, d in pairs)
     d2h = sum(len(r) * 8 for r in rb)
     _emit({"metric": "instances/s, 64 (6,50) instances per batched call", "value": 64 / tb,
@@ -374,8 +393,10 @@ def bench_batch(args):
            "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "u64", "data": "synthetic",
            "config": {"workload": "64 (6,50) instances, seeds 1000..1063, 32 plain + 32 planted (25 ones)",
-                      "l2": "pass buffers of ~37 GB, larger than L2"},
+                      "path": "direct pass: every instance's lists, one join launch over the 4096 classes "
+                              "of all 64 instances, one verification launch"},
            "sequential": {"value": 64 / ts, "unit": "instances/s", "ms_per_step": ts * 1e3},
+           "streaming_batch": {"value": 64 / tst, "unit": "instances/s", "ms_per_step": tst * 1e3},
            "speedup_vs_sequential": ts / tb,
            "e2e": {"value": 64 / tb, "unit": "instances/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h}})
@@ -521,19 +542,22 @@ def bench_10_90(args):
 
 def bench_profile_part(args):
     """One solve of the (9,80) bench instance over residue-class part 0 of
-    4096 with a 1500 MB device budget: a few passes of a few hundred MB, the
-    case the ncu captures under profiles/ are taken on."""
+    4096: the case the ncu captures under profiles/ are taken on.  The
+    direct pass (default) builds the full inner lists, then joins 1/4096 of
+    the classes in one launch; ``--path 0`` takes the streaming pass with a
+    1500 MB budget (a few passes of a few hundred MB)."""
     import paper_2507_05045_gb300 as msp
     from paper_2507_05045_gb300 import build
     build.build()
     A, d, _ = mi.generate(M_, N_, SEED)
-    with msp.Instance(A, d, class_part=(0, 4096), memory_budget=1500 << 20, profiling=True) as inst:
+    kw = {"plan": {"direct": 0}, "memory_budget": 1500 << 20} if args.path == 0 else {"plan": {"direct": 1}}
+    with msp.Instance(A, d, class_part=(0, 4096), profiling=True, **kw) as inst:
         t0 = time.perf_counter()
         inst.solve_all()
         dt = time.perf_counter() - t0
         st = inst.stats()
     _emit({"config": {"workload": f"({M_},{N_}) plain instance seed {SEED}, classes part 0 of 4096, "
-                                  "1500 MB budget"},
+                                  f"{st['path']} pass"},
            "seconds": dt, "passes": st["passes"], "records_done": st["records_done"],
            "class_bits": st["class_bits"], "digit_bits": st["digit_bits"], "kernels": st["kernels"]})
 

@@ -200,6 +200,15 @@ MSP_API void msp_free_solutions(uint64_t *masks);
 MSP_API int msp_solve_batch(const int32_t *const *A, const int32_t *const *d, int m, int n, int count,
                     uint64_t **masks, size_t *offsets);
 
+/* msp_solve_batch with the enumeration path chosen: path 1 = the direct pass
+ * (MSP_ERANGE when the instances do not fit it), 0 = the streaming pass,
+ * -1 = the direct pass when it fits, else streaming (what msp_solve_batch
+ * does).  On the direct pass every instance's lists are built, then the
+ * residue classes of all instances are joined by one launch (per 2^20
+ * classes) and every match is verified by one more. */
+MSP_API int msp_solve_batch_path(const int32_t *const *A, const int32_t *const *d, int m, int n, int count,
+                                 int path, uint64_t **masks, size_t *offsets);
+
 /* Serving: a request queue whose instances share the device.  Requests are
  * admitted while their next residue pass fits the memory budget, and the
  * passes of admitted requests are interleaved on several streams. */

@@ -131,8 +131,17 @@ struct DirectSide {
   int no;
 };
 
-struct DirectPass {
+// One instance of a direct pass (device table: one entry for a single
+// solve, one per instance of a batch of the same (m, n)).
+struct DirectInst {
   DirectSide side[2];
+};
+
+struct DirectPass {
+  const DirectInst *inst;  // [ninst]
+  uint32_t ninst;
+  int no[2];              // outer subsets per side (the same for every instance)
+  uint32_t class_bits;    // a match is tagged instance << class_bits | class
   uint32_t cmask;
   uint32_t c0;            // first class of the launch
   uint32_t nclass;        // classes of the launch
@@ -304,13 +313,14 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
   uint32_t *const wbm = reinterpret_cast<uint32_t *>(et + kDW * 32);
   uint32_t *const wq = wbm + kDW * 32;      // [kDW][kQueue]
   uint32_t *const wtot = wq + kDW * kQueue;
-  const int noL = p.side[0].no, noR = p.side[1].no;
+  const int noL = p.no[0], noR = p.no[1];
   // per-class totals, double-buffered by class parity: class i accumulates
   // into slot i & 1 before its first barrier, and the other slot is reset
   // after that barrier, once every thread has read it for class i - 1
   __shared__ unsigned long long s_fill[2][2];
   __shared__ uint32_t s_bad[2];
   __shared__ uint32_t s_item;
+  __shared__ DirectInst s_inst;
 
   const uint32_t ln = lane_id(), wp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kDW * 32; i += kDT) wbm[i] = 0u;
@@ -402,17 +412,19 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
     return qn >= 32u;
   };
   const uint32_t cmask = p.cmask;
-  const uint32_t *__restrict__ ioffL = p.side[0].ioff;
-  const uint32_t *__restrict__ ioffR = p.side[1].ioff;
-  const uint32_t *__restrict__ ikeyL = p.side[0].ikey;
-  const uint32_t *__restrict__ ikeyR = p.side[1].ikey;
-  const uint32_t nitems = (p.nclass + p.chunk - 1) / p.chunk;
+  const uint32_t *__restrict__ ioffL = nullptr;
+  const uint32_t *__restrict__ ioffR = nullptr;
+  const uint32_t *__restrict__ ikeyL = nullptr;
+  const uint32_t *__restrict__ ikeyR = nullptr;
+  const uint32_t per_inst = (p.nclass + p.chunk - 1) / p.chunk;  // work items per instance
+  const uint32_t nitems = per_inst * p.ninst;
   unsigned long long my_records = 0;  // thread 0 only
-  // bucket bounds [ioff[w], ioff[w + 1]) of this lane's outer subset for a
-  // class, on both sides (0, 0 past the outer list)
+  // this lane's outer subset (key, class) on both sides, for the current
+  // instance; bucket bounds [ioff[w], ioff[w + 1]) of it for a class (0, 0
+  // past the outer list)
   const int el = wp * 32 + ln;
-  const uint32_t kaL = el < noL ? p.side[0].okey[el] : 0u, kaR = el < noR ? p.side[1].okey[el] : 0u;
-  const uint32_t clL = el < noL ? p.side[0].ocls[el] : 0u, clR = el < noR ? p.side[1].ocls[el] : 0u;
+  uint32_t kaL = 0, kaR = 0, clL = 0, clR = 0;
+  uint32_t cur_inst = 0xffffffffu;
   uint32_t pfL0 = 0, pfL1 = 0, pfR0 = 0, pfR1 = 0;
   auto load_bounds = [&](uint32_t r) {
     pfL0 = pfL1 = pfR0 = pfR1 = 0u;
@@ -430,11 +442,28 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
   uint32_t par = 0;                   // parity of the block's class count
 
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(p.work, 1u);
+    if (threadIdx.x == 0) {
+      const uint32_t it = atomicAdd(p.work, 1u);
+      s_item = it;
+      if (it < nitems) s_inst = p.inst[it / per_inst];
+    }
     __syncthreads();
     const uint32_t item = s_item;
     if (item >= nitems) break;
-    const uint32_t rb = item * p.chunk, re = min(p.nclass, rb + p.chunk);
+    const uint32_t ii = item / per_inst;
+    if (ii != cur_inst) {  // block-uniform
+      cur_inst = ii;
+      ioffL = s_inst.side[0].ioff;
+      ioffR = s_inst.side[1].ioff;
+      ikeyL = s_inst.side[0].ikey;
+      ikeyR = s_inst.side[1].ikey;
+      kaL = el < noL ? s_inst.side[0].okey[el] : 0u;
+      clL = el < noL ? s_inst.side[0].ocls[el] : 0u;
+      kaR = el < noR ? s_inst.side[1].okey[el] : 0u;
+      clR = el < noR ? s_inst.side[1].ocls[el] : 0u;
+    }
+    const uint32_t tag = ii << p.class_bits;
+    const uint32_t rb = (item - ii * per_inst) * p.chunk, re = min(p.nclass, rb + p.chunk);
     for (uint32_t ri = rb; ri < re; ++ri, par ^= 1u) {
       const uint32_t r = (p.c0 + ri) & cmask;
       // ---- bucket of this warp's outer subsets (lane = subset), loaded
@@ -524,10 +553,10 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
             for (int b = 0; b < kBatch; ++b) {
               const uint32_t k = key[b];
               const bool pass = ((okm >> b) & 1u) && ((fw[b] >> ((k >> fshift) & 31u)) & 1u);
-              if (defer(pass, k)) drain_probe(r);
+              if (defer(pass, k)) drain_probe(tag | r);
             }
           });
-          if (qn) drain_probe(r);
+          if (qn) drain_probe(tag | r);
         }
       }
       __syncthreads();
@@ -540,23 +569,29 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
 // -------------------------------------------------------------------------
 // Recovery and exact verification of the matched (class, key) pairs.
 // -------------------------------------------------------------------------
-constexpr int kVT = 128;
+constexpr int kVT = 512;  // one thread per outer subset of each side
 constexpr int kVCand = 512;
 
-struct DirectVerify {
+// The lists of one instance that verification reads.
+struct DirectVerifyInst {
   DirectSide side[2];
   const uint32_t *imask[2];  // inner subset masks (bucketed order)
   const uint32_t *omask[2];  // outer subset masks
   const uint64_t *ovec[2];   // [no][4] packed row sums of the outer subsets
   const uint64_t *icol[2];   // [qi][4] packed column vectors of the inner quarters
+  uint64_t dvec[4];          // packed right-hand side
+};
+
+struct DirectVerify {
+  const DirectVerifyInst *inst;  // [ninst], indexed by a match's tag
   int qi[2];
   int col_o[2], col_i[2];    // first column of each quarter
   int W;                     // packed words in use
-  uint64_t dvec[4];
+  uint32_t class_bits;
   uint32_t cmask;
   const uint32_t *match_key;
-  const uint32_t *match_cls;
-  uint64_t *sol;             // [sol_cap][2]
+  const uint32_t *match_cls; // instance << class_bits | class
+  uint64_t *sol;             // [sol_cap][3]: mask low word, high word, instance
   unsigned long long *sol_count;
   uint64_t sol_cap;
   unsigned long long *pairs;
@@ -573,29 +608,41 @@ __device__ __forceinline__ void put_bits(uint64_t &lo, uint64_t &hi, uint64_t bi
 }
 
 __global__ void __launch_bounds__(kVT) direct_verify_kernel(DirectVerify v) {
+  static_assert(kVT >= kOuterMax, "one pass over the outer subsets");
   __shared__ uint2 cand[2][kVCand];
   __shared__ uint32_t ncand[2];
   __shared__ uint64_t scol[2][kInnerMax][4];
   const uint32_t key = v.match_key[blockIdx.x];
-  const uint32_t r = v.match_cls[blockIdx.x];
+  const uint32_t tagged = v.match_cls[blockIdx.x];
+  const uint32_t ii = tagged >> v.class_bits;
+  const uint32_t r = tagged & v.cmask;
+  const DirectVerifyInst &vi = v.inst[ii];
   if (threadIdx.x < 2) ncand[threadIdx.x] = 0;
   for (int i = threadIdx.x; i < 2 * kInnerMax * 4; i += kVT) {
     const int s = i / (kInnerMax * 4), j = (i / 4) % kInnerMax, w = i % 4;
-    scol[s][j][w] = j < v.qi[s] ? v.icol[s][j * 4 + w] : 0ull;
+    scol[s][j][w] = j < v.qi[s] ? vi.icol[s][j * 4 + w] : 0ull;
   }
   __syncthreads();
-  for (int s = 0; s < 2; ++s) {
-    const DirectSide &sd = v.side[s];
-    for (int a = threadIdx.x; a < sd.no; a += kVT) {
-      const uint32_t w = (r - sd.ocls[a]) & v.cmask;
-      const uint32_t b0 = sd.ioff[w], b1 = sd.ioff[w + 1];
-      const uint32_t ka = sd.okey[a];
-      for (uint32_t j = b0; j < b1; ++j)
-        if (jkey(ka + sd.ikey[j]) == key) {
+  // thread a scans the bucket of outer subset a on both sides; the bucket
+  // bounds of the two sides are loaded together
+  {
+    const int a = threadIdx.x;
+    uint32_t b0[2] = {0u, 0u}, b1[2] = {0u, 0u}, ka[2] = {0u, 0u};
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+      if (a < vi.side[s].no) {
+        const uint32_t w = (r - vi.side[s].ocls[a]) & v.cmask;
+        b0[s] = vi.side[s].ioff[w];
+        b1[s] = vi.side[s].ioff[w + 1];
+        ka[s] = vi.side[s].okey[a];
+      }
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+      for (uint32_t j = b0[s]; j < b1[s]; ++j)
+        if (jkey(ka[s] + vi.side[s].ikey[j]) == key) {
           const uint32_t slot = atomicAdd(&ncand[s], 1u);
           if (slot < kVCand) cand[s][slot] = make_uint2(static_cast<uint32_t>(a), j);
         }
-    }
   }
   __syncthreads();
   const uint32_t nL = min(ncand[0], static_cast<uint32_t>(kVCand));
@@ -608,8 +655,8 @@ __global__ void __launch_bounds__(kVT) direct_verify_kernel(DirectVerify v) {
   for (uint32_t pi = threadIdx.x; pi < np; pi += kVT) {
     const uint2 l = cand[0][pi / nR], rr = cand[1][pi % nR];
     uint64_t vec[4];
-    for (int w = 0; w < 4; ++w) vec[w] = v.ovec[0][l.x * 4 + w] + v.ovec[1][rr.x * 4 + w];
-    const uint32_t mL = v.imask[0][l.y], mR = v.imask[1][rr.y];
+    for (int w = 0; w < 4; ++w) vec[w] = vi.ovec[0][l.x * 4 + w] + vi.ovec[1][rr.x * 4 + w];
+    const uint32_t mL = vi.imask[0][l.y], mR = vi.imask[1][rr.y];
     for (uint32_t b = mL; b; b &= b - 1) {
       const int j = __ffs(b) - 1;
       for (int w = 0; w < 4; ++w) vec[w] += scol[0][j][w];
@@ -619,17 +666,18 @@ __global__ void __launch_bounds__(kVT) direct_verify_kernel(DirectVerify v) {
       for (int w = 0; w < 4; ++w) vec[w] += scol[1][j][w];
     }
     bool eq = true;
-    for (int w = 0; w < v.W; ++w) eq &= vec[w] == v.dvec[w];
+    for (int w = 0; w < v.W; ++w) eq &= vec[w] == vi.dvec[w];
     if (eq) {
       uint64_t lo = 0, hi = 0;
-      put_bits(lo, hi, v.omask[0][l.x], v.col_o[0]);
+      put_bits(lo, hi, vi.omask[0][l.x], v.col_o[0]);
       put_bits(lo, hi, mL, v.col_i[0]);
-      put_bits(lo, hi, v.omask[1][rr.x], v.col_o[1]);
+      put_bits(lo, hi, vi.omask[1][rr.x], v.col_o[1]);
       put_bits(lo, hi, mR, v.col_i[1]);
       const unsigned long long slot = atomicAdd(v.sol_count, 1ull);
       if (slot < v.sol_cap) {
-        v.sol[2 * slot] = lo;
-        v.sol[2 * slot + 1] = hi;
+        v.sol[3 * slot] = lo;
+        v.sol[3 * slot + 1] = hi;
+        v.sol[3 * slot + 2] = ii;
       }
     }
   }
@@ -660,7 +708,7 @@ template <int TB>
 cudaError_t launch_direct_join_tb(const DirectPass &p, cudaStream_t s) {
   static size_t attr = 0;
   static int per_sm = 0, sms = 0;
-  const size_t smem = direct_smem_bytes(TB, p.side[0].no, p.side[1].no);
+  const size_t smem = direct_smem_bytes(TB, p.no[0], p.no[1]);
   if (smem > attr) {
     cudaError_t e = cudaFuncSetAttribute(direct_join_kernel<TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
@@ -676,13 +724,15 @@ cudaError_t launch_direct_join_tb(const DirectPass &p, cudaStream_t s) {
     }
     per_sm = n;
   }
-  // work items of up to 32 consecutive classes (neighbouring classes share
-  // bucket-offset and inner-key sectors), at least four per resident block
+  // work items of up to 4 consecutive classes (neighbouring classes share
+  // bucket-offset and inner-key sectors; short items keep the blocks
+  // evenly loaded to the end of the launch)
   const uint32_t resident = static_cast<uint32_t>(std::max(1, per_sm * sms));
   DirectPass q = p;
-  q.chunk = std::max<uint32_t>(1, std::min<uint32_t>(32, p.nclass / (4 * resident)));
-  const uint32_t nitems = (q.nclass + q.chunk - 1) / q.chunk;
-  const int blocks = static_cast<int>(std::max<uint32_t>(1, std::min<uint32_t>(nitems, resident)));
+  q.chunk = static_cast<uint32_t>(
+      std::max<uint64_t>(1, std::min<uint64_t>(4, (uint64_t)p.nclass * p.ninst / (4 * resident))));
+  const uint64_t nitems = (uint64_t)((q.nclass + q.chunk - 1) / q.chunk) * q.ninst;
+  const int blocks = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(nitems, resident)));
   direct_join_kernel<TB><<<blocks, kDT, smem, s>>>(q);
   return cudaGetLastError();
 }
@@ -743,42 +793,46 @@ size_t direct_footprint(const DirectPlan &d) {
   return static_cast<size_t>(b);
 }
 
-// Solves `inst` on the direct pass.  Returns MSP_OK with res (unsorted
-// two-word masks), kDirectFallback when another path must solve it (out of
-// memory for the inner lists, a class beyond the kernel's bounds, a match
-// list or candidate list overflow), or an error status.
-int solve_direct(msp_instance *inst, const DirectPlan &dp, const Plan &kp, size_t budget, Prof &prof,
-                 std::vector<uint64_t> &res) {
-  const int m = inst->m, n = inst->n;
-  msp_stats &st = inst->stats;
-  cudaStream_t s = inst->stream;
+namespace {
+
+// Host and device lists of one instance of a direct pass.
+struct DirectLists {
+  std::vector<uint32_t> okey[2], ocls[2], omask[2];
+  std::vector<uint64_t> ovec[2];
+  uint64_t dvec[4] = {0, 0, 0, 0};
+  uint32_t *ikey[2] = {nullptr, nullptr}, *imask[2] = {nullptr, nullptr}, *ioff[2] = {nullptr, nullptr};
+  uint64_t *icol[2] = {nullptr, nullptr};
+  uint32_t *d_okey[2] = {nullptr, nullptr}, *d_ocls[2] = {nullptr, nullptr}, *d_omask[2] = {nullptr, nullptr};
+  uint64_t *d_ovec[2] = {nullptr, nullptr};
+};
+
+struct Copier {
+  msp_stats *st;
+  cudaStream_t s;
+  cudaError_t h2d(void *dst, const void *src, size_t b) {
+    if (st) st->h2d_bytes += b;
+    return cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, s);
+  }
+  cudaError_t d2h(void *dst, const void *src, size_t b) {
+    if (st) st->d2h_bytes += b;
+    return cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, s);
+  }
+};
+
+// S0 + S1 + S2 of one instance: column keys and classes, the outer lists
+// (host, at most 2^9 subsets each), the inner lists bucketed by class
+// (device: count, offsets, scatter).  `cnt` and `scantmp` are scratch of
+// 2^B + 1 and (2^B + 1) / 4096 + 1 entries, shared by successive calls.
+int build_direct_lists(const int32_t *A, const int32_t *d, int m, int n, const DirectPlan &dp, const Plan &kp,
+                       DevAlloc &da, Copier &cp, Prof &prof, uint32_t *cnt, uint32_t *scantmp, DirectLists &L) {
+  cudaStream_t s = cp.s;
   const uint32_t M = 1u << dp.B, cmask = M - 1u;
-  if (direct_footprint(dp) > budget) return kDirectFallback;
-
-  auto h2d = [&](void *dst, const void *hsrc, size_t b) {
-    st.h2d_bytes += b;
-    return cudaMemcpyAsync(dst, hsrc, b, cudaMemcpyHostToDevice, s);
-  };
-  auto d2h = [&](void *hdst, const void *dsrc, size_t b) {
-    st.d2h_bytes += b;
-    return cudaMemcpyAsync(hdst, dsrc, b, cudaMemcpyDeviceToHost, s);
-  };
-
-  st.quarter[0] = dp.qo[0];
-  st.quarter[1] = dp.qo[1];
-  st.quarter[2] = dp.qi[0];
-  st.quarter[3] = dp.qi[1];
-  st.class_bits = dp.B;
-  st.class_rows = dp.t;
-  st.digit_bits = 0;
-
-  // ---- S0: per-column key, class and packed vector ----
   std::vector<uint32_t> ck(n), cc(n);
   std::vector<uint64_t> pc((size_t)n * 4, 0);
   for (int j = 0; j < n; ++j) {
     uint32_t k = 0, c = 0;
     for (int i = 0; i < m; ++i) {
-      const uint32_t a = static_cast<uint32_t>(inst->A[(size_t)i * n + j]);
+      const uint32_t a = static_cast<uint32_t>(A[(size_t)i * n + j]);
       k += static_cast<uint32_t>(kp.w_row[i]) * a;
       if (i < dp.t) c += kp.c_row[i] * a;
       pc[(size_t)j * 4 + i / 4] += static_cast<uint64_t>(a) << (16 * (i % 4));
@@ -787,53 +841,40 @@ int solve_direct(msp_instance *inst, const DirectPlan &dp, const Plan &kp, size_
     cc[j] = c;
   }
   uint32_t kd = 0, cd = 0;
-  uint64_t dvec[4] = {0, 0, 0, 0};
   for (int i = 0; i < m; ++i) {
-    const uint32_t di = static_cast<uint32_t>(inst->d[i]);
+    const uint32_t di = static_cast<uint32_t>(d[i]);
     kd += static_cast<uint32_t>(kp.w_row[i]) * di;
     if (i < dp.t) cd += kp.c_row[i] * di;
-    dvec[i / 4] += static_cast<uint64_t>(di) << (16 * (i % 4));
+    L.dvec[i / 4] += static_cast<uint64_t>(di) << (16 * (i % 4));
   }
-
-  // ---- S1 (outer quarters): every subset on the host, at most 2^10 ----
-  std::vector<uint32_t> okey[2], ocls[2], omask[2];
-  std::vector<uint64_t> ovec[2];
   for (int sd = 0; sd < 2; ++sd) {
     const int q = dp.qo[sd], c0 = dp.col_o[sd];
     const uint32_t no = 1u << q;
-    okey[sd].resize(no);
-    ocls[sd].resize(no);
-    omask[sd].resize(no);
-    ovec[sd].assign((size_t)no * 4, 0);
+    L.okey[sd].resize(no);
+    L.ocls[sd].resize(no);
+    L.omask[sd].resize(no);
+    L.ovec[sd].assign((size_t)no * 4, 0);
     for (uint32_t u = 0; u < no; ++u) {
       uint32_t k = 0, c = 0;
       for (int j = 0; j < q; ++j)
         if (u >> j & 1u) {
           k += ck[c0 + j];
           c += cc[c0 + j];
-          for (int w = 0; w < 4; ++w) ovec[sd][(size_t)u * 4 + w] += pc[(size_t)(c0 + j) * 4 + w];
+          for (int w = 0; w < 4; ++w) L.ovec[sd][(size_t)u * 4 + w] += pc[(size_t)(c0 + j) * 4 + w];
         }
-      okey[sd][u] = sd ? kd - k : k;
-      ocls[sd][u] = (sd ? cd - c : c) & cmask;
-      omask[sd][u] = u;
+      L.okey[sd][u] = sd ? kd - k : k;
+      L.ocls[sd][u] = (sd ? cd - c : c) & cmask;
+      L.omask[sd][u] = u;
     }
   }
-
-  DevAlloc da(s);
-  // ---- S1 + S2 (inner quarters): Gray walk, counting sort by class ----
-  uint32_t *ikey[2], *imask[2], *ioff[2];
-  uint64_t *icol[2];
-  uint32_t *cnt, *scantmp;
-  CK(da.get(&cnt, (size_t)M + 1));
-  CK(da.get(&scantmp, ((size_t)M + 1 + 4095) / 4096 + 1));
   for (int sd = 0; sd < 2; ++sd) {
     const int q = dp.qi[sd], c0 = dp.col_i[sd];
     const uint64_t ni = uint64_t(1) << q;
-    CK(da.get(&ikey[sd], ni));
-    CK(da.get(&imask[sd], ni));
-    CK(da.get(&ioff[sd], (size_t)M + 1));
-    CK(da.get(&icol[sd], (size_t)std::max(q, 1) * 4));
-    if (q) CK(h2d(icol[sd], pc.data() + (size_t)c0 * 4, sizeof(uint64_t) * 4 * q));
+    CK(da.get(&L.ikey[sd], ni));
+    CK(da.get(&L.imask[sd], ni));
+    CK(da.get(&L.ioff[sd], (size_t)M + 1));
+    CK(da.get(&L.icol[sd], (size_t)std::max(q, 1) * 4));
+    if (q) CK(cp.h2d(L.icol[sd], pc.data() + (size_t)c0 * 4, sizeof(uint64_t) * 4 * q));
     InnerGen g{};
     for (int j = 0; j < q; ++j) {
       g.ck[j] = ck[c0 + j];
@@ -847,47 +888,66 @@ int solve_direct(msp_instance *inst, const DirectPlan &dp, const Plan &kp, size_
     const unsigned blocks = static_cast<unsigned>(std::min<uint64_t>((nchunks + 255) / 256, 1u << 20));
     CK(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * M, s));
     LAUNCH(MSP_K_BUCKET, 1, 0, (direct_inner_count_kernel<<<blocks, 256, 0, s>>>(g, c, nchunks, cnt), cudaGetLastError()));
-    LAUNCH(MSP_K_BUCKET, 3, 0, launch_scan_u32(cnt, ioff[sd], M, scantmp, s));
-    CK(cudaMemcpyAsync(cnt, ioff[sd], sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, s));
+    LAUNCH(MSP_K_BUCKET, 3, 0, launch_scan_u32(cnt, L.ioff[sd], M, scantmp, s));
+    CK(cudaMemcpyAsync(cnt, L.ioff[sd], sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, s));
     LAUNCH(MSP_K_BUCKET, 1, 0,
-           (direct_inner_scatter_kernel<<<blocks, 256, 0, s>>>(g, c, nchunks, cnt, ikey[sd], imask[sd]),
+           (direct_inner_scatter_kernel<<<blocks, 256, 0, s>>>(g, c, nchunks, cnt, L.ikey[sd], L.imask[sd]),
             cudaGetLastError()));
   }
-  da.free1(cnt, sizeof(uint32_t) * ((size_t)M + 1));
-
-  uint32_t *d_okey[2], *d_ocls[2], *d_omask[2];
-  uint64_t *d_ovec[2];
   for (int sd = 0; sd < 2; ++sd) {
-    const size_t no = okey[sd].size();
-    CK(da.get(&d_okey[sd], no));
-    CK(da.get(&d_ocls[sd], no));
-    CK(da.get(&d_omask[sd], no));
-    CK(da.get(&d_ovec[sd], no * 4));
-    CK(h2d(d_okey[sd], okey[sd].data(), 4 * no));
-    CK(h2d(d_ocls[sd], ocls[sd].data(), 4 * no));
-    CK(h2d(d_omask[sd], omask[sd].data(), 4 * no));
-    CK(h2d(d_ovec[sd], ovec[sd].data(), 8 * 4 * no));
+    const size_t no = L.okey[sd].size();
+    CK(da.get(&L.d_okey[sd], no));
+    CK(da.get(&L.d_ocls[sd], no));
+    CK(da.get(&L.d_omask[sd], no));
+    CK(da.get(&L.d_ovec[sd], no * 4));
+    CK(cp.h2d(L.d_okey[sd], L.okey[sd].data(), 4 * no));
+    CK(cp.h2d(L.d_ocls[sd], L.ocls[sd].data(), 4 * no));
+    CK(cp.h2d(L.d_omask[sd], L.omask[sd].data(), 4 * no));
+    CK(cp.h2d(L.d_ovec[sd], L.ovec[sd].data(), 8 * 4 * no));
   }
+  return MSP_OK;
+}
 
-  // ---- C1: row-1 candidate pairs (the metric's unit of work) ----
-  {
-    int32_t *d_a1;
-    unsigned __int128 *d_dp;
-    unsigned long long *d_c1;
-    const int d1 = inst->d[0];
-    CK(da.get(&d_a1, n));
-    CK(da.get(&d_dp, 2 * ((size_t)d1 + 1)));
-    CK(da.get(&d_c1, 2));
-    CK(h2d(d_a1, inst->A.data(), sizeof(int32_t) * n));
-    LAUNCH(MSP_K_C1, 1, 0, (c1_dp_kernel<<<1, 1024, 0, s>>>(d_a1, n, d1, d_dp, d_c1), cudaGetLastError()));
-    unsigned long long c1h[2];
-    CK(d2h(c1h, d_c1, sizeof(c1h)));
-    CK(cudaStreamSynchronize(s));
-    st.row1_candidates_lo = c1h[0];
-    st.row1_candidates_hi = c1h[1];
+// The class joins and the verification of the instances `lists` (all of one
+// (m, n)), over the residue classes [c_begin, c_end) of each.  Solutions go
+// to out[instance] as two words each (unsorted); st (may be null) receives
+// passes, records, matches and pairs verified.  Returns MSP_OK,
+// kDirectFallback, or an error status.
+int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint32_t c_begin, uint32_t c_end,
+               DevAlloc &da, Copier &cp, Prof &prof, msp_stats *st, const volatile int *cancel,
+               std::vector<std::vector<uint64_t>> &out) {
+  cudaStream_t s = cp.s;
+  const uint32_t M = 1u << dp.B, cmask = M - 1u;
+  const uint32_t K = static_cast<uint32_t>(lists.size());
+  out.assign(K, {});
+  if (K == 0 || c_begin >= c_end) return MSP_OK;
+  std::vector<DirectInst> tab(K);
+  std::vector<DirectVerifyInst> vtab(K);
+  for (uint32_t k = 0; k < K; ++k) {
+    const DirectLists &L = lists[k];
+    for (int sd = 0; sd < 2; ++sd) {
+      DirectSide &ds = tab[k].side[sd];
+      ds.okey = L.d_okey[sd];
+      ds.ocls = L.d_ocls[sd];
+      ds.ikey = L.ikey[sd];
+      ds.ioff = L.ioff[sd];
+      ds.no = static_cast<int>(L.okey[sd].size());
+      DirectVerifyInst &vi = vtab[k];
+      vi.side[sd] = ds;
+      vi.imask[sd] = L.imask[sd];
+      vi.omask[sd] = L.d_omask[sd];
+      vi.ovec[sd] = L.d_ovec[sd];
+      vi.icol[sd] = L.icol[sd];
+    }
+    for (int w = 0; w < 4; ++w) vtab[k].dvec[w] = L.dvec[w];
   }
+  DirectInst *d_tab;
+  DirectVerifyInst *d_vtab;
+  CK(da.get(&d_tab, K));
+  CK(da.get(&d_vtab, K));
+  CK(cp.h2d(d_tab, tab.data(), sizeof(DirectInst) * K));
+  CK(cp.h2d(d_vtab, vtab.data(), sizeof(DirectVerifyInst) * K));
 
-  // ---- the class joins ----
   uint32_t *match_key, *match_cls;
   unsigned long long *match_count, *records;
   unsigned int *work, *err;
@@ -900,19 +960,12 @@ int solve_direct(msp_instance *inst, const DirectPlan &dp, const Plan &kp, size_
   CK(cudaMemsetAsync(records, 0, sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(err, 0, sizeof(unsigned int), s));
 
-  if (inst->part >= inst->parts) return fail(MSP_EINVAL, "class part must be below the number of parts");
-  const uint32_t c_begin = static_cast<uint32_t>((uint64_t)M * inst->part / inst->parts);
-  const uint32_t c_end = static_cast<uint32_t>((uint64_t)M * (inst->part + 1) / inst->parts);
-  st.classes_total = M;
-  st.classes_done = c_end - c_begin;
   DirectPass p{};
-  for (int sd = 0; sd < 2; ++sd) {
-    p.side[sd].okey = d_okey[sd];
-    p.side[sd].ocls = d_ocls[sd];
-    p.side[sd].ikey = ikey[sd];
-    p.side[sd].ioff = ioff[sd];
-    p.side[sd].no = static_cast<int>(okey[sd].size());
-  }
+  p.inst = d_tab;
+  p.ninst = K;
+  p.no[0] = tab[0].side[0].no;
+  p.no[1] = tab[0].side[1].no;
+  p.class_bits = static_cast<uint32_t>(dp.B);
   p.cmask = cmask;
   p.insert_cap = (5u << dp.TB) / 8;  // about 5 of the 8 slots of a bucket
   p.match_key = match_key;
@@ -921,98 +974,221 @@ int solve_direct(msp_instance *inst, const DirectPlan &dp, const Plan &kp, size_
   p.match_cap = kDirectMatchCap;
   p.records = records;
   p.error = err;
-  // launches of at most 2^20 classes (a bounded kernel time; cancellation
-  // is checked between launches)
-  const uint32_t per_launch = 1u << 20;
-  const uint32_t nlaunch = (c_end - c_begin + per_launch - 1) / per_launch;
-  CK(da.get(&work, std::max<uint32_t>(1, nlaunch)));
-  CK(cudaMemsetAsync(work, 0, sizeof(unsigned int) * std::max<uint32_t>(1, nlaunch), s));
-  const double per_class_in = 4.0 * (p.side[0].no + p.side[1].no);
+  // launches of at most 2^20 classes in all (a bounded kernel time;
+  // cancellation is checked between launches)
+  const uint32_t ncls = c_end - c_begin;
+  const uint32_t per_launch = std::max<uint32_t>(1, (1u << 20) / K);
+  const uint32_t nlaunch = (ncls + per_launch - 1) / per_launch;
+  CK(da.get(&work, nlaunch));
+  CK(cudaMemsetAsync(work, 0, sizeof(unsigned int) * nlaunch, s));
+  const double per_class_in = 4.0 * (p.no[0] + p.no[1]);
   int passes = 0;
   for (uint32_t li = 0; li < nlaunch; ++li) {
-    if (inst->cancel && *inst->cancel) return fail(MSP_ECANCELED, "request canceled");
+    if (cancel && *cancel) return fail(MSP_ECANCELED, "request canceled");
     p.c0 = c_begin + li * per_launch;
     p.nclass = std::min(per_launch, c_end - p.c0);
     p.work = work + li;
     // algorithmic bytes: 4 per record (its inner key) plus one bucket offset
-    // per outer subset and class; the records are counted on the device
+    // per outer subset and class; the exact record count replaces this
+    // estimate once the solve ends
     const double rec_est =
-        (double)p.nclass * (std::ldexp(1.0, dp.cols[0] - dp.B) + std::ldexp(1.0, dp.cols[1] - dp.B));
-    LAUNCH(MSP_K_DIRECT, 1, static_cast<uint64_t>(4.0 * rec_est + per_class_in * p.nclass),
+        (double)K * p.nclass * (std::ldexp(1.0, dp.cols[0] - dp.B) + std::ldexp(1.0, dp.cols[1] - dp.B));
+    LAUNCH(MSP_K_DIRECT, 1, static_cast<uint64_t>(4.0 * rec_est + per_class_in * p.nclass * K),
            launch_direct_join(dp.TB, p, s));
     ++passes;
   }
   unsigned long long nmatch = 0, nrec = 0;
   unsigned int err_h = 0;
-  CK(d2h(&nmatch, match_count, sizeof(nmatch)));
-  CK(d2h(&nrec, records, sizeof(nrec)));
-  CK(d2h(&err_h, err, sizeof(err_h)));
+  CK(cp.d2h(&nmatch, match_count, sizeof(nmatch)));
+  CK(cp.d2h(&nrec, records, sizeof(nrec)));
+  CK(cp.d2h(&err_h, err, sizeof(err_h)));
   CK(cudaStreamSynchronize(s));
   prof.flush();
-  st.passes = passes;
-  st.records_done = nrec;
-  st.key_matches = nmatch;
-  if (err_h || nmatch > kDirectMatchCap) return kDirectFallback;
-
-  if (nmatch > 0) {
-    DirectVerify v{};
-    for (int sd = 0; sd < 2; ++sd) {
-      v.side[sd] = p.side[sd];
-      v.imask[sd] = imask[sd];
-      v.omask[sd] = d_omask[sd];
-      v.ovec[sd] = d_ovec[sd];
-      v.icol[sd] = icol[sd];
-      v.qi[sd] = dp.qi[sd];
-      v.col_o[sd] = dp.col_o[sd];
-      v.col_i[sd] = dp.col_i[sd];
-    }
-    v.W = dp.W;
-    for (int w = 0; w < 4; ++w) v.dvec[w] = dvec[w];
-    v.cmask = cmask;
-    v.match_key = match_key;
-    v.match_cls = match_cls;
-    unsigned long long *cnts;
-    unsigned int *ovf;
-    CK(da.get(&cnts, 2));
-    CK(da.get(&ovf, 1));
-    v.sol_count = cnts;
-    v.pairs = cnts + 1;
-    v.overflow = ovf;
-    uint64_t cap = 1u << 16;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      uint64_t *sol;
-      CK(da.get(&sol, 2 * cap));
-      v.sol = sol;
-      v.sol_cap = cap;
-      CK(cudaMemsetAsync(cnts, 0, 2 * sizeof(unsigned long long), s));
-      CK(cudaMemsetAsync(ovf, 0, sizeof(unsigned int), s));
-      LAUNCH(MSP_K_VERIFY, 1, 0,
-             (direct_verify_kernel<<<static_cast<unsigned>(nmatch), kVT, 0, s>>>(v), cudaGetLastError()));
-      unsigned long long hc[2];
-      unsigned int ovf_h = 0;
-      CK(d2h(hc, cnts, sizeof(hc)));
-      CK(d2h(&ovf_h, ovf, sizeof(ovf_h)));
-      CK(cudaStreamSynchronize(s));
-      if (ovf_h) return kDirectFallback;
-      st.pairs_verified = hc[1];
-      if (hc[0] <= cap) {
-        res.resize(2 * hc[0]);
-        if (hc[0]) {
-          CK(d2h(res.data(), sol, sizeof(uint64_t) * 2 * hc[0]));
-          CK(cudaStreamSynchronize(s));
-        }
-        break;
-      }
-      if (hc[0] > (1ull << 28)) return fail(MSP_EOVERFLOW, "more than 2^28 solutions");
-      cap = hc[0];
-    }
+  if (st) {
+    st->passes = passes;
+    st->records_done = nrec;
+    st->key_matches = nmatch;
+    if (prof.on) st->kernel_bytes[MSP_K_DIRECT] = 4 * nrec + static_cast<uint64_t>(per_class_in * ncls * K);
   }
-  if (prof.on) st.kernel_bytes[MSP_K_DIRECT] = 4 * nrec + static_cast<uint64_t>(per_class_in * (c_end - c_begin));
+  if (err_h || nmatch > kDirectMatchCap) return kDirectFallback;
+  if (nmatch == 0) return MSP_OK;
+
+  DirectVerify v{};
+  v.inst = d_vtab;
+  for (int sd = 0; sd < 2; ++sd) {
+    v.qi[sd] = dp.qi[sd];
+    v.col_o[sd] = dp.col_o[sd];
+    v.col_i[sd] = dp.col_i[sd];
+  }
+  v.W = dp.W;
+  v.class_bits = static_cast<uint32_t>(dp.B);
+  v.cmask = cmask;
+  v.match_key = match_key;
+  v.match_cls = match_cls;
+  unsigned long long *cnts;
+  unsigned int *ovf;
+  CK(da.get(&cnts, 2));
+  CK(da.get(&ovf, 1));
+  v.sol_count = cnts;
+  v.pairs = cnts + 1;
+  v.overflow = ovf;
+  uint64_t cap = 1u << 16;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    uint64_t *sol;
+    CK(da.get(&sol, 3 * cap));
+    v.sol = sol;
+    v.sol_cap = cap;
+    CK(cudaMemsetAsync(cnts, 0, 2 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ovf, 0, sizeof(unsigned int), s));
+    LAUNCH(MSP_K_VERIFY, 1, 0,
+           (direct_verify_kernel<<<static_cast<unsigned>(nmatch), kVT, 0, s>>>(v), cudaGetLastError()));
+    unsigned long long hc[2];
+    unsigned int ovf_h = 0;
+    CK(cp.d2h(hc, cnts, sizeof(hc)));
+    CK(cp.d2h(&ovf_h, ovf, sizeof(ovf_h)));
+    CK(cudaStreamSynchronize(s));
+    if (ovf_h) return kDirectFallback;
+    if (st) st->pairs_verified = hc[1];
+    if (hc[0] <= cap) {
+      std::vector<uint64_t> h(3 * hc[0]);
+      if (hc[0]) {
+        CK(cp.d2h(h.data(), sol, sizeof(uint64_t) * 3 * hc[0]));
+        CK(cudaStreamSynchronize(s));
+      }
+      for (uint64_t i = 0; i < hc[0]; ++i) {
+        const uint64_t k = h[3 * i + 2];
+        if (k >= K) return fail(MSP_ECUDA, "verification produced an invalid instance tag");
+        out[k].push_back(h[3 * i]);
+        out[k].push_back(h[3 * i + 1]);
+      }
+      break;
+    }
+    if (hc[0] > (1ull << 28)) return fail(MSP_EOVERFLOW, "more than 2^28 solutions");
+    cap = hc[0];
+  }
+  return MSP_OK;
+}
+
+}  // namespace
+
+// Solves `inst` on the direct pass.  Returns MSP_OK with res (unsorted
+// two-word masks), kDirectFallback when another path must solve it (out of
+// memory for the inner lists, a class beyond the kernel's bounds, a match
+// list or candidate list overflow), or an error status.
+int solve_direct(msp_instance *inst, const DirectPlan &dp, const Plan &kp, size_t budget, Prof &prof,
+                 std::vector<uint64_t> &res) {
+  const int n = inst->n;
+  msp_stats &st = inst->stats;
+  cudaStream_t s = inst->stream;
+  const uint32_t M = 1u << dp.B;
+  if (direct_footprint(dp) > budget) return kDirectFallback;
+  if (inst->part >= inst->parts) return fail(MSP_EINVAL, "class part must be below the number of parts");
+
+  st.quarter[0] = dp.qo[0];
+  st.quarter[1] = dp.qo[1];
+  st.quarter[2] = dp.qi[0];
+  st.quarter[3] = dp.qi[1];
+  st.class_bits = dp.B;
+  st.class_rows = dp.t;
+  st.digit_bits = 0;
+
+  DevAlloc da(s);
+  Copier cp{&st, s};
+  std::vector<DirectLists> lists(1);
+  {
+    uint32_t *cnt, *scantmp;
+    CK(da.get(&cnt, (size_t)M + 1));
+    CK(da.get(&scantmp, ((size_t)M + 1 + 4095) / 4096 + 1));
+    const int rc = build_direct_lists(inst->A.data(), inst->d.data(), inst->m, n, dp, kp, da, cp, prof, cnt,
+                                      scantmp, lists[0]);
+    if (rc != MSP_OK) return rc;
+    da.free1(cnt, sizeof(uint32_t) * ((size_t)M + 1));
+  }
+
+  // ---- C1: row-1 candidate pairs (the metric's unit of work) ----
+  {
+    int32_t *d_a1;
+    unsigned __int128 *d_dp;
+    unsigned long long *d_c1;
+    const int d1 = inst->d[0];
+    CK(da.get(&d_a1, n));
+    CK(da.get(&d_dp, 2 * ((size_t)d1 + 1)));
+    CK(da.get(&d_c1, 2));
+    CK(cp.h2d(d_a1, inst->A.data(), sizeof(int32_t) * n));
+    LAUNCH(MSP_K_C1, 1, 0, (c1_dp_kernel<<<1, 1024, 0, s>>>(d_a1, n, d1, d_dp, d_c1), cudaGetLastError()));
+    unsigned long long c1h[2];
+    CK(cp.d2h(c1h, d_c1, sizeof(c1h)));
+    CK(cudaStreamSynchronize(s));
+    st.row1_candidates_lo = c1h[0];
+    st.row1_candidates_hi = c1h[1];
+  }
+
+  const uint32_t c_begin = static_cast<uint32_t>((uint64_t)M * inst->part / inst->parts);
+  const uint32_t c_end = static_cast<uint32_t>((uint64_t)M * (inst->part + 1) / inst->parts);
+  st.classes_total = M;
+  st.classes_done = c_end - c_begin;
+  std::vector<std::vector<uint64_t>> out;
+  const int rc = run_direct(lists, dp, c_begin, c_end, da, cp, prof, &st, inst->cancel, out);
+  if (rc != MSP_OK) return rc;
+  res = std::move(out[0]);
   st.device_bytes = da.peak;
   da.release();
   CK(cudaStreamSynchronize(s));
   prof.flush();
-  (void)m;
+  return MSP_OK;
+}
+
+// msp_solve_batch on the direct pass: every instance's lists, then one join
+// launch (per 2^20 classes) over the classes of all instances and one
+// verification launch over all matches.  raw[k]: unsorted two-word masks of
+// instance k.  Returns MSP_OK, kDirectFallback or an error status.
+int solve_batch_direct(const int32_t *const *A, const int32_t *const *d, int m, int n, int count,
+                       std::vector<std::vector<uint64_t>> &raw, cudaStream_t s, size_t budget) {
+  raw.assign(count, {});
+  const DirectPlan dp = make_direct_plan(m, n, -1);
+  if (!dp.ok) return kDirectFallback;
+  const Plan kp = make_plan(m, n);
+  const uint32_t M = 1u << dp.B;
+  // feasible right-hand sides only
+  std::vector<int> idx;
+  for (int k = 0; k < count; ++k) {
+    bool feasible = true;
+    for (int i = 0; i < m && feasible; ++i) {
+      int64_t rs = 0;
+      for (int j = 0; j < n; ++j) rs += A[k][(size_t)i * n + j];
+      feasible = d[k][i] <= rs;
+    }
+    if (feasible) idx.push_back(k);
+  }
+  const uint32_t K = static_cast<uint32_t>(idx.size());
+  if (K == 0) return MSP_OK;
+  // tags instance << B | class must fit 32 bits; lists of all instances
+  // must fit the budget
+  if ((uint64_t)K << dp.B > (1ull << 32)) return kDirectFallback;
+  const double per_inst = 8.0 * (std::ldexp(1.0, dp.qi[0]) + std::ldexp(1.0, dp.qi[1])) +
+                          8.0 * (std::ldexp(1.0, dp.B) + 1) + (64 << 10);
+  if (per_inst * K + (double)direct_footprint(dp) > (double)budget) return kDirectFallback;
+
+  DevAlloc da(s);
+  Copier cp{nullptr, s};
+  msp_stats scratch{};
+  Prof prof;
+  prof.s = s;
+  prof.st = &scratch;
+  std::vector<DirectLists> lists(K);
+  uint32_t *cnt, *scantmp;
+  CK(da.get(&cnt, (size_t)M + 1));
+  CK(da.get(&scantmp, ((size_t)M + 1 + 4095) / 4096 + 1));
+  for (uint32_t k = 0; k < K; ++k) {
+    const int rc = build_direct_lists(A[idx[k]], d[idx[k]], m, n, dp, kp, da, cp, prof, cnt, scantmp, lists[k]);
+    if (rc != MSP_OK) return rc;
+  }
+  std::vector<std::vector<uint64_t>> out;
+  const int rc = run_direct(lists, dp, 0, M, da, cp, prof, nullptr, nullptr, out);
+  if (rc != MSP_OK) return rc;
+  for (uint32_t k = 0; k < K; ++k) raw[idx[k]] = std::move(out[k]);
+  da.release();
+  CK(cudaStreamSynchronize(s));
   return MSP_OK;
 }
 

@@ -85,6 +85,9 @@ constexpr uint64_t kDirectMatchCap = 1u << 23;  // matched (class, key) pairs he
 struct Prof;
 int solve_direct(msp_instance *inst, const DirectPlan &dp, const Plan &kp, size_t budget, Prof &prof,
                  std::vector<uint64_t> &res);
+// msp_solve_batch on the direct pass (MSP_OK, kDirectFallback or an error).
+int solve_batch_direct(const int32_t *const *A, const int32_t *const *d, int m, int n, int count,
+                       std::vector<std::vector<uint64_t>> &raw, cudaStream_t s, size_t budget);
 // Device memory a solve may use: the instance budget, else 85% of what is
 // free (counting the stream-ordered pool's unused memory as free).
 size_t solve_budget(const msp_instance *inst, size_t already_held);

@@ -930,7 +930,13 @@ void msp_free_solutions(uint64_t *masks) { std::free(masks); }
 
 int msp_solve_batch(const int32_t *const *A, const int32_t *const *d, int m, int n, int count,
                     uint64_t **masks, size_t *offsets) {
+  return msp_solve_batch_path(A, d, m, n, count, -1, masks, offsets);
+}
+
+int msp_solve_batch_path(const int32_t *const *A, const int32_t *const *d, int m, int n, int count, int path,
+                         uint64_t **masks, size_t *offsets) {
   if (!A || !d || !masks || !offsets || count < 0) return fail(MSP_EINVAL, "null argument");
+  if (path < -1 || path > 1) return fail(MSP_ERANGE, "path must be -1, 0 or 1");
   *masks = nullptr;
   offsets[0] = 0;
   for (int k = 0; k < count; ++k) {
@@ -945,7 +951,14 @@ int msp_solve_batch(const int32_t *const *A, const int32_t *const *d, int m, int
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
     return fail(MSP_ECUDA, "cudaStreamCreate failed");
   std::vector<std::vector<uint64_t>> raw;
-  const int rc = msp::solve_batch_impl(A, d, m, n, count, raw, s, 0);
+  int rc = msp::kDirectFallback;
+  if (path != 0) {
+    msp_instance probe;  // only for the memory budget of the device
+    cudaGetDevice(&probe.device);
+    rc = msp::solve_batch_direct(A, d, m, n, count, raw, s, msp::solve_budget(&probe, 0));
+    if (rc == msp::kDirectFallback && path == 1) rc = fail(MSP_ERANGE, "the batch does not fit the direct pass");
+  }
+  if (rc == msp::kDirectFallback) rc = msp::solve_batch_impl(A, d, m, n, count, raw, s, 0);
   cudaStreamSynchronize(s);
   cudaStreamDestroy(s);
   if (rc != MSP_OK) return rc;

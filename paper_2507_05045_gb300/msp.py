@@ -25,7 +25,7 @@ EXPORTED_SYMBOLS = (
     "msp_create", "msp_destroy", "msp_set_stream", "msp_set_memory_budget", "msp_solve_all",
     "msp_get_stats", "msp_free_solutions", "msp_set_profiling", "msp_set_option", "msp_solve_batch", "msp_server_create", "msp_submit",
     "msp_poll", "msp_cancel", "msp_server_destroy", "msp_last_error", "msp_version",
-    "msp_solve_small_noalloc", "msp_device_name",
+    "msp_solve_small_noalloc", "msp_device_name", "msp_solve_batch_path",
 )
 
 # msp_set_option codes (include/msp.h)
@@ -110,6 +110,9 @@ def load_library(path: str | None = None):
         lib.msp_free_solutions.restype = None
         lib.msp_solve_batch.argtypes = [ctypes.POINTER(i32p), ctypes.POINTER(i32p), ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.POINTER(u64p), ctypes.POINTER(ctypes.c_size_t)]
+        lib.msp_solve_batch_path.argtypes = [ctypes.POINTER(i32p), ctypes.POINTER(i32p), ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, ctypes.POINTER(u64p),
+                                             ctypes.POINTER(ctypes.c_size_t)]
         lib.msp_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
         lib.msp_submit.argtypes = [vp, i32p, i32p, ctypes.c_int, ctypes.c_int, u64p]
         lib.msp_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(u64p), ctypes.POINTER(ctypes.c_size_t),
@@ -227,8 +230,9 @@ def solve_all(A, d, **kw):
         return inst.solve_all()
 
 
-def solve_batch(instances):
-    """Solve a list of (A, d) pairs of one (m, n) with ``msp_solve_batch``."""
+def solve_batch(instances, path: int = -1):
+    """Solve a list of (A, d) pairs of one (m, n) with ``msp_solve_batch_path``
+    (path -1: direct pass when it fits, 1: direct pass, 0: streaming pass)."""
     lib = load_library()
     if not instances:
         return []
@@ -246,7 +250,7 @@ def solve_batch(instances):
         dp[k] = dpp
     ptr = ctypes.POINTER(ctypes.c_uint64)()
     offs = (ctypes.c_size_t * (len(instances) + 1))()
-    _check(lib.msp_solve_batch(Ap, dp, m, n, len(instances), ctypes.byref(ptr), offs))
+    _check(lib.msp_solve_batch_path(Ap, dp, m, n, len(instances), int(path), ctypes.byref(ptr), offs))
     words = (n + 63) // 64
     total = offs[len(instances)]
     flat = _take_masks(lib, ptr, total, words)

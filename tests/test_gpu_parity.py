@@ -139,13 +139,36 @@ def test_row1_candidate_count_matches_counting_dp(msp, plan):
         assert st["row1_candidates"] == oracle.row1_candidates(A, d)
 
 
-def test_config_6_50_batch(msp):
+@pytest.mark.parametrize("path", [-1, 1, 0])
+def test_config_6_50_batch(msp, path):
+    # one batched call over 64 instances: direct pass (default and forced)
+    # and streaming pass
     entries = load_golden("sols_6_50_batch.json")
-    got = msp.solve_batch([(A, d) for _, A, d, _, _ in entries])
+    got = msp.solve_batch([(A, d) for _, A, d, _, _ in entries], path=path)
     for (e, A, d, x, sols), g in zip(entries, got):
         assert g == sols, e["seed"]
         if x is not None:
             assert mi.mask_of(x) in g
+
+
+def test_batch_mixed_feasibility_and_tags(msp):
+    # infeasible right-hand sides, planted and plain instances and small-K
+    # instances with many solutions in one batch: every instance keeps its
+    # own solution set (match and solution tags carry the instance)
+    insts = []
+    for k in range(12):
+        A, d, _ = mi.generate(4, 30, 300 + k, K=[100, 5, 3][k % 3], planted=bool(k % 2), h=15)
+        if k % 4 == 3:
+            d = d.copy()
+            d[2] = A[2].sum() + 1
+        insts.append((A, d))
+    want = [oracle.mitm(A, d) for A, d in insts]
+    # the heavy small-K instances may exceed the direct verification's
+    # candidate lists, so the automatic choice may fall back to streaming
+    for path in (-1, 0):
+        assert msp.solve_batch(insts, path=path) == want
+    light = [insts[k] for k in range(12) if k % 3 == 0]
+    assert msp.solve_batch(light, path=1) == [want[k] for k in range(12) if k % 3 == 0]
 
 
 @pytest.mark.parametrize("plan", PATHS)
