@@ -52,14 +52,17 @@ def parse():
     ap.add_argument("--m", type=int, default=M_)
     ap.add_argument("--n", type=int, default=N_)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", choices=["9_80", "batch_6_50", "serving", "10_90_part", "profile_part"],
+    ap.add_argument("--config", choices=["9_80", "batch_6_50", "serving", "10_90_part", "profile_part",
+                                         "profile_small"],
                     default="9_80",
                     help="9_80 (default): the headline exhaustive solve; batch_6_50: 64 (6,50) "
                          "instances in one batched call vs one at a time; serving: the mixed Poisson "
                          "request stream through the server vs sequential solving; 10_90_part: one "
                          "seeded 1/64 of the residue classes of a (10,90) instance; profile_part: "
-                         "the case the ncu captures use (the (9,80) instance of the default "
-                         "workload over 1/4096 of its residue classes, one solve)")
+                         "the case the ncu traffic captures use (the (9,80) instance of the default "
+                         "workload over 1/4096 of its residue classes, one solve); profile_small: one "
+                         "direct-pass solve of a (7,60) instance (lists of 8 MB), the case of the "
+                         "full-section captures")
     ap.add_argument("--path", type=int, default=1, choices=[0, 1],
                     help="profile_part: 1 = direct pass, 0 = streaming pass")
     ap.add_argument("--requests", type=int, default=256)
@@ -200,10 +203,10 @@ def traffic_per_launch(kernel, alg_bytes_per_launch):
     import hashlib
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        src = open(os.path.join(ROOT, t["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest() != t["source_sha256"]:
-            return None
         k = t["kernels"][kernel]
+        src = open(os.path.join(ROOT, k["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != k["source_sha256"]:
+            return None
         return alg_bytes_per_launch * k["dram_bytes"] / k["algorithmic_bytes"]
     except Exception:
         return None
@@ -562,6 +565,23 @@ def bench_profile_part(args):
            "class_bits": st["class_bits"], "digit_bits": st["digit_bits"], "kernels": st["kernels"]})
 
 
+def bench_profile_small(args):
+    """One direct-pass solve of the plain (7,60) instance of seed 7: inner
+    lists of 8 MB and 2^31 records, the small case the full-section ncu
+    captures use."""
+    import paper_2507_05045_gb300 as msp
+    from paper_2507_05045_gb300 import build
+    build.build()
+    A, d, _ = mi.generate(7, 60, 7)
+    with msp.Instance(A, d, plan={"direct": 1}, profiling=True) as inst:
+        t0 = time.perf_counter()
+        sols = inst.solve_all()
+        dt = time.perf_counter() - t0
+        st = inst.stats()
+    _emit({"config": {"workload": "(7,60) plain instance seed 7, direct pass"}, "seconds": dt,
+           "solutions": len(sols), "records_done": st["records_done"], "kernels": st["kernels"]})
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_init(args)
@@ -580,6 +600,9 @@ def main():
         elif args.config == "profile_part":
             if rank == 0:
                 bench_profile_part(args)
+        elif args.config == "profile_small":
+            if rank == 0:
+                bench_profile_small(args)
         else:
             native(args, world, rank, local, pg)
     finally:

@@ -147,7 +147,7 @@ MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
  *                        whose partitions would not fit shared memory is
  *                        solved on the exact path)
  *   MSP_OPT_INNER_BITS   the inner quarter of each side (Q3 of L, Q4 of R)
- *                        gets B + value columns (at most 23, never fewer than
+ *                        gets B + value columns (at most 27, never fewer than
  *                        the even split), so an inner residue bucket holds
  *                        about 2^value elements: the run of records one outer
  *                        element expands to in the scatter, in [0, 12]

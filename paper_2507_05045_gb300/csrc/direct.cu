@@ -974,10 +974,13 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
   p.match_cap = kDirectMatchCap;
   p.records = records;
   p.error = err;
-  // launches of at most 2^20 classes in all (a bounded kernel time;
-  // cancellation is checked between launches)
+  // launches of about 2^32 records (15 ms) and at most 2^20 classes in all:
+  // a bounded kernel time, so cancellation (checked between launches) and
+  // the kernels of other requests on higher-priority streams get their turn
   const uint32_t ncls = c_end - c_begin;
-  const uint32_t per_launch = std::max<uint32_t>(1, (1u << 20) / K);
+  const double rec_per_class = std::ldexp(1.0, dp.cols[0] - dp.B) + std::ldexp(1.0, dp.cols[1] - dp.B);
+  const uint32_t per_launch = static_cast<uint32_t>(std::max<double>(
+      1.0, std::min<double>(std::ldexp(1.0, 32) / rec_per_class, (double)(1u << 20)) / K));
   const uint32_t nlaunch = (ncls + per_launch - 1) / per_launch;
   CK(da.get(&work, nlaunch));
   CK(cudaMemsetAsync(work, 0, sizeof(unsigned int) * nlaunch, s));
@@ -991,8 +994,7 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
     // algorithmic bytes: 4 per record (its inner key) plus one bucket offset
     // per outer subset and class; the exact record count replaces this
     // estimate once the solve ends
-    const double rec_est =
-        (double)K * p.nclass * (std::ldexp(1.0, dp.cols[0] - dp.B) + std::ldexp(1.0, dp.cols[1] - dp.B));
+    const double rec_est = (double)K * p.nclass * rec_per_class;
     LAUNCH(MSP_K_DIRECT, 1, static_cast<uint64_t>(4.0 * rec_est + per_class_in * p.nclass * K),
            launch_direct_join(dp.TB, p, s));
     ++passes;

@@ -1,13 +1,17 @@
 // Serving loop of libmsp: msp_server_create / msp_submit / msp_poll.
 //
-// Requests of mixed (m, n) wait in a FIFO queue.  A request is admitted as
-// soon as a worker slot is free and its device footprint (quarter lists plus
-// one residue pass, footprint_estimate) fits in what the budget has left;
+// Requests of mixed (m, n) wait in a queue in arrival order.  A request is
+// admitted as soon as a worker slot is free and its device footprint
+// (footprint_estimate) fits in what the budget has left; a large request
+// (more than about 2^32 half-pair records) also waits until no other large
+// one is running;
 // the footprint also caps that request's pass buffers, so admitted requests
 // never exceed the budget together.  Each worker runs its request's residue
 // passes on its own CUDA stream, so the passes of all admitted requests are
 // interleaved on the device, and requests that arrive while others run are
-// admitted as slots and memory free up (continuous batching).
+// admitted as slots and memory free up (continuous batching).  Small
+// requests run on high-priority streams, so they overtake the kernels of
+// large ones at the next launch boundary.
 #include "host_internal.h"
 
 #include <atomic>
@@ -28,6 +32,7 @@ struct Request {
   int m = 0, n = 0;
   std::vector<int32_t> A, d;
   size_t footprint = 0;
+  bool urgent = false;  // small request: runs on the worker's high-priority stream
   ReqState state = kQueued;
   int rc = MSP_OK;
   std::string err;
@@ -51,14 +56,21 @@ struct msp_server {
   std::vector<std::thread> workers;
   bool stop = false;
   uint64_t next_id = 1;
+  int large_running = 0;  // admitted requests that are not small
 };
 
 namespace {
 
 void worker_loop(msp_server *srv) {
   cudaSetDevice(srv->device);
-  cudaStream_t stream = nullptr;
-  cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+  // Two streams: small requests on the high-priority one, so that their
+  // kernels take SMs ahead of the (bounded, ~15 ms) launches of large
+  // requests running on the other workers' low-priority streams.
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  cudaStream_t stream = nullptr, urgent_stream = nullptr;
+  cudaStreamCreateWithPriority(&stream, cudaStreamNonBlocking, least);
+  cudaStreamCreateWithPriority(&urgent_stream, cudaStreamNonBlocking, greatest);
   for (;;) {
     Request *rq = nullptr;
     {
@@ -67,9 +79,14 @@ void worker_loop(msp_server *srv) {
         if (srv->stop) {
           lk.unlock();
           if (stream) cudaStreamDestroy(stream);
+          if (urgent_stream) cudaStreamDestroy(urgent_stream);
           return;
         }
-        // FIFO admission: the head request runs once its footprint fits.
+        // Admission in arrival order, by size: a small request runs as soon
+        // as a worker and its footprint are free; a large one (whose kernels
+        // fill the GPU by themselves) waits until no other large request is
+        // running, so large requests run one after another at full speed
+        // while small ones pass them.
         while (!srv->queue.empty()) {
           auto it = srv->reqs.find(srv->queue.front());
           if (it == srv->reqs.end() || it->second->state != kQueued) {
@@ -78,16 +95,24 @@ void worker_loop(msp_server *srv) {
           }
           break;
         }
-        if (!srv->queue.empty()) {
-          Request *head = srv->reqs[srv->queue.front()];
-          if (srv->in_use == 0 || srv->in_use + head->footprint <= srv->budget) {
-            srv->queue.pop_front();
-            rq = head;
+        bool large_waits = srv->large_running > 0;
+        for (auto qi = srv->queue.begin(); qi != srv->queue.end(); ++qi) {
+          auto it = srv->reqs.find(*qi);
+          if (it == srv->reqs.end() || it->second->state != kQueued) continue;
+          Request *cand = it->second;
+          if (!cand->urgent && large_waits) continue;
+          if (srv->in_use == 0 || srv->in_use + cand->footprint <= srv->budget) {
+            srv->queue.erase(qi);
+            rq = cand;
             rq->state = kRunning;
             srv->in_use += rq->footprint;
+            if (!rq->urgent) ++srv->large_running;
             break;
           }
+          // the oldest large request keeps its turn until memory frees up
+          if (!cand->urgent) large_waits = true;
         }
+        if (rq) break;
         srv->cv.wait(lk);
       }
     }
@@ -96,7 +121,7 @@ void worker_loop(msp_server *srv) {
     inst.n = rq->n;
     inst.A = rq->A;
     inst.d = rq->d;
-    inst.stream = stream;
+    inst.stream = rq->urgent ? urgent_stream : stream;
     inst.own_stream = false;
     inst.budget = rq->footprint;
     inst.device = srv->device;
@@ -109,6 +134,7 @@ void worker_loop(msp_server *srv) {
     {
       std::lock_guard<std::mutex> lk(srv->mu);
       srv->in_use -= rq->footprint;
+      if (!rq->urgent) --srv->large_running;
       rq->rc = rc;
       rq->err = err;
       rq->masks = masks;
@@ -169,6 +195,7 @@ int msp_submit(msp_server *srv, const int32_t *A, const int32_t *d, int m, int n
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     rq->footprint = msp::footprint_estimate(m, n, srv->budget / static_cast<size_t>(srv->max_inflight));
+    rq->urgent = n <= 62;  // at most about 2^32 half-pair records
     if (rq->footprint > srv->budget) {
       delete rq;
       return msp::fail(MSP_ENOMEM, "request footprint exceeds the server budget");

@@ -59,13 +59,13 @@ Plan make_plan(int m, int n, const PlanChoice &ch) {
   p.t = std::min(p.t, m);
   // Uneven halves: the inner quarter of each side (Q3 of L, Q4 of R) takes
   // columns from the outer one until an inner residue bucket holds about 16
-  // elements (2^(q_inner - B)), at most 2^23 of them, so that every outer
+  // elements (2^(q_inner - B)), at most 2^27 of them, so that every outer
   // element of a scatter window expands to a run of consecutive inner keys.
   // |L| and |R| do not change, nor do the classes and partitions.
   const int inner_bits = ch.inner >= 0 ? ch.inner : 4;
   for (int side = 0; side < 2; ++side) {
     const int tot = p.q[side] + p.q[side + 2];
-    const int want = std::min({std::max(p.q[side + 2], p.B + inner_bits), 23, tot - 1});
+    const int want = std::min({std::max(p.q[side + 2], p.B + inner_bits), 27, tot - 1});
     if (want > p.q[side + 2]) {
       p.q[side + 2] = want;
       p.q[side] = tot - want;

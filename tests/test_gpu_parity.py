@@ -393,6 +393,20 @@ def test_direct_pass_on_skewed_classes(msp):
     assert solve(msp, A, d, {"direct": 0})[0] == want
 
 
+def test_streaming_pass_with_large_inner_quarters(msp):
+    # the streaming pass with inner quarters of 27 columns (the shape the
+    # (10,90) configuration takes): the same solution set as the direct pass
+    A, d, x = mi.generate(8, 70, 81, planted=True, h=35)
+    plan = {"class_bits": 22, "digit_bits": 1, "inner_bits": 5, "direct": 0}
+    got, st = solve(msp, A, d, plan)
+    assert max(st["quarter"][2], st["quarter"][3]) == 27
+    want, st_d = solve(msp, A, d, {"direct": 1})
+    assert st_d["path"] == "direct"
+    assert got == want
+    assert mi.mask_of(x) in got
+    _check_solutions_exact(A, d, got)
+
+
 def test_plan_options_are_validated(msp):
     A, d, _ = mi.generate(4, 30, 1)
     for bad in [{"class_bits": 24}, {"digit_bits": 13}, {"inner_bits": -2}, {"table_bits": 16},
