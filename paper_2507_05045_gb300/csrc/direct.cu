@@ -52,7 +52,6 @@ namespace msp {
 namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr uint32_t kEmpty = 0xffffffffu;  // empty slot of the shared table
 constexpr int kDT = 512;                  // threads per join block
 constexpr int kDW = kDT / 32;             // warps per join block
 constexpr int kOuterMax = 32 * kDW;       // outer subsets per side: one per lane of each warp
@@ -61,10 +60,6 @@ constexpr int kGenChunk = 6;              // Gray walk of 2^6 subsets per thread
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
-// Join key of a record: keys equal to the empty marker share the next value
-// (both sides apply it, so equal sums still meet; the rare extra matches are
-// removed by the exact check).
-__device__ __forceinline__ uint32_t jkey(uint32_t k) { return min(k, 0xfffffffeu); }
 
 struct InnerGen {
   uint32_t ck[kInnerMax];  // 32-bit key of each column (row sums weighted by w_i)
@@ -121,6 +116,78 @@ __global__ void direct_inner_scatter_kernel(InnerGen g, int c, uint64_t nchunks,
       imask[pos] = mask;
     });
   }
+}
+
+// The inner quarter of one side of one instance of a batch: its column
+// tables and its lists.
+struct InnerSeg {
+  InnerGen g;
+  uint32_t *cnt;    // [2^B] counts, then insertion cursors
+  uint32_t *ioff;   // [2^B + 1] bucket starts
+  uint32_t *ikey;   // [2^q] keys in bucket order
+  uint32_t *imask;  // [2^q] subset masks in bucket order
+};
+
+// Counts (scatter = false) or bucket placement (scatter = true) of the inner
+// subsets of every segment of a batch: thread t walks chunk t mod
+// chunks_per_seg of segment t / chunks_per_seg.
+template <bool kScatter>
+__global__ void direct_inner_batch_kernel(const InnerSeg *segs, int c, uint64_t chunks_per_seg, uint64_t total) {
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t sg = t / chunks_per_seg;
+    const InnerSeg &S = segs[sg];
+    const uint32_t base = static_cast<uint32_t>((t - sg * chunks_per_seg) << c);
+    if constexpr (kScatter) {
+      walk_chunk(S.g, base, c, [&](uint32_t mask, uint32_t k, uint32_t r) {
+        const uint32_t pos = atomicAdd(S.cnt + r, 1u);
+        S.ikey[pos] = k;
+        S.imask[pos] = mask;
+      });
+    } else {
+      walk_chunk(S.g, base, c, [&](uint32_t, uint32_t, uint32_t r) { atomicAdd(S.cnt + r, 1u); });
+    }
+  }
+}
+
+// Bucket starts of every segment of a batch, one block per segment:
+// ioff = exclusive scan of the counts (ioff[M] = 2^q), and the counts are
+// replaced by the starts (the insertion cursors of the placement pass).
+__global__ void __launch_bounds__(1024) direct_inner_offsets_kernel(const InnerSeg *segs, uint32_t M) {
+  __shared__ uint32_t wt[32];
+  const InnerSeg &S = segs[blockIdx.x];
+  const uint32_t per = (M + blockDim.x - 1) / blockDim.x;
+  const uint32_t b0 = min(M, threadIdx.x * per), b1 = min(M, b0 + per);
+  uint32_t sum = 0;
+  for (uint32_t i = b0; i < b1; ++i) sum += S.cnt[i];
+  // block exclusive scan of the per-thread sums
+  const uint32_t ln = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, o);
+    if (ln >= static_cast<uint32_t>(o)) x += y;
+  }
+  if (ln == 31) wt[wp] = x;
+  __syncthreads();
+  if (wp == 0) {
+    uint32_t t = ln < nw ? wt[ln] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, t, o);
+      if (ln >= static_cast<uint32_t>(o)) t += y;
+    }
+    if (ln < nw) wt[ln] = t;
+  }
+  __syncthreads();
+  uint32_t run = x - sum + (wp ? wt[wp - 1] : 0u);
+  for (uint32_t i = b0; i < b1; ++i) {
+    const uint32_t cnt = S.cnt[i];
+    S.ioff[i] = run;
+    S.cnt[i] = run;
+    run += cnt;
+  }
+  if (threadIdx.x == blockDim.x - 1) S.ioff[M] = wt[nw - 1];
 }
 
 struct DirectSide {
@@ -277,7 +344,7 @@ __device__ __forceinline__ void group_records(uint32_t st, uint32_t len, uint32_
         const bool more = i0 + 32u * kBatch < send;  // warp-uniform
         if (more) fetch(i0 + 32u * kBatch, rn, kn, okn);
 #pragma unroll
-        for (int b = 0; b < kBatch; ++b) key[b] = jkey(kc[b] + rc[b]);
+        for (int b = 0; b < kBatch; ++b) key[b] = kc[b] + rc[b];
         f(okc, key);
         if (more) {
 #pragma unroll
@@ -290,7 +357,7 @@ __device__ __forceinline__ void group_records(uint32_t st, uint32_t len, uint32_
       } else {
         fetch(i0, rc, kc, okc);
 #pragma unroll
-        for (int b = 0; b < kBatch; ++b) key[b] = jkey(kc[b] + rc[b]);
+        for (int b = 0; b < kBatch; ++b) key[b] = kc[b] + rc[b];
         f(okc, key);
       }
     }
@@ -299,7 +366,6 @@ __device__ __forceinline__ void group_records(uint32_t st, uint32_t len, uint32_
 
 template <int TB>
 __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
-  constexpr uint32_t TS = 1u << TB;
   constexpr int kBB = TB - 3;        // bucket bits
   constexpr int hshift = 32 - kBB;   // home bucket = top kBB key bits
   constexpr int fshift = 32 - (TB + 3);
@@ -639,7 +705,7 @@ __global__ void __launch_bounds__(kVT) direct_verify_kernel(DirectVerify v) {
 #pragma unroll
     for (int s = 0; s < 2; ++s)
       for (uint32_t j = b0[s]; j < b1[s]; ++j)
-        if (jkey(ka[s] + vi.side[s].ikey[j]) == key) {
+        if (ka[s] + vi.side[s].ikey[j] == key) {
           const uint32_t slot = atomicAdd(&ncand[s], 1u);
           if (slot < kVCand) cand[s][slot] = make_uint2(static_cast<uint32_t>(a), j);
         }
@@ -823,9 +889,12 @@ struct Copier {
 // (host, at most 2^9 subsets each), the inner lists bucketed by class
 // (device: count, offsets, scatter).  `cnt` and `scantmp` are scratch of
 // 2^B + 1 and (2^B + 1) / 4096 + 1 entries, shared by successive calls.
-int build_direct_lists(const int32_t *A, const int32_t *d, int m, int n, const DirectPlan &dp, const Plan &kp,
-                       DevAlloc &da, Copier &cp, Prof &prof, uint32_t *cnt, uint32_t *scantmp, DirectLists &L) {
-  cudaStream_t s = cp.s;
+// S0 + S1 on the host for one instance: the column keys and classes, the
+// outer lists (at most 2^9 subsets each), the packed right-hand side, and
+// the column tables g[side] and packed column vectors icol[side] of the
+// inner quarters.
+void prep_direct_host(const int32_t *A, const int32_t *d, int m, int n, const DirectPlan &dp, const Plan &kp,
+                      DirectLists &L, InnerGen g[2], std::vector<uint64_t> icol[2]) {
   const uint32_t M = 1u << dp.B, cmask = M - 1u;
   std::vector<uint32_t> ck(n), cc(n);
   std::vector<uint64_t> pc((size_t)n * 4, 0);
@@ -869,20 +938,39 @@ int build_direct_lists(const int32_t *A, const int32_t *d, int m, int n, const D
   }
   for (int sd = 0; sd < 2; ++sd) {
     const int q = dp.qi[sd], c0 = dp.col_i[sd];
+    g[sd] = InnerGen{};
+    for (int j = 0; j < q; ++j) {
+      g[sd].ck[j] = ck[c0 + j];
+      g[sd].cc[j] = cc[c0 + j];
+    }
+    g[sd].q = q;
+    g[sd].neg = sd;
+    g[sd].cmask = cmask;
+    icol[sd].assign(pc.begin() + (size_t)c0 * 4, pc.begin() + (size_t)(c0 + q) * 4);
+    icol[sd].resize((size_t)std::max(q, 1) * 4, 0);
+  }
+}
+
+// S0 + S1 + S2 of one instance: host preparation, then the inner lists
+// bucketed by class on the device (count, offsets, scatter).  `cnt` and
+// `scantmp` are scratch of 2^B + 1 and (2^B + 1) / 4096 + 1 entries, shared
+// by successive calls.
+int build_direct_lists(const int32_t *A, const int32_t *d, int m, int n, const DirectPlan &dp, const Plan &kp,
+                       DevAlloc &da, Copier &cp, Prof &prof, uint32_t *cnt, uint32_t *scantmp, DirectLists &L) {
+  cudaStream_t s = cp.s;
+  const uint32_t M = 1u << dp.B;
+  InnerGen gs[2];
+  std::vector<uint64_t> icol[2];
+  prep_direct_host(A, d, m, n, dp, kp, L, gs, icol);
+  for (int sd = 0; sd < 2; ++sd) {
+    const int q = dp.qi[sd];
     const uint64_t ni = uint64_t(1) << q;
     CK(da.get(&L.ikey[sd], ni));
     CK(da.get(&L.imask[sd], ni));
     CK(da.get(&L.ioff[sd], (size_t)M + 1));
-    CK(da.get(&L.icol[sd], (size_t)std::max(q, 1) * 4));
-    if (q) CK(cp.h2d(L.icol[sd], pc.data() + (size_t)c0 * 4, sizeof(uint64_t) * 4 * q));
-    InnerGen g{};
-    for (int j = 0; j < q; ++j) {
-      g.ck[j] = ck[c0 + j];
-      g.cc[j] = cc[c0 + j];
-    }
-    g.q = q;
-    g.neg = sd;
-    g.cmask = cmask;
+    CK(da.get(&L.icol[sd], icol[sd].size()));
+    CK(cp.h2d(L.icol[sd], icol[sd].data(), sizeof(uint64_t) * icol[sd].size()));
+    const InnerGen &g = gs[sd];
     const int c = std::min(q, kGenChunk);
     const uint64_t nchunks = ni >> c;
     const unsigned blocks = static_cast<unsigned>(std::min<uint64_t>((nchunks + 255) / 256, 1u << 20));
@@ -904,6 +992,108 @@ int build_direct_lists(const int32_t *A, const int32_t *d, int m, int n, const D
     CK(cp.h2d(L.d_ocls[sd], L.ocls[sd].data(), 4 * no));
     CK(cp.h2d(L.d_omask[sd], L.omask[sd].data(), 4 * no));
     CK(cp.h2d(L.d_ovec[sd], L.ovec[sd].data(), 8 * 4 * no));
+  }
+  return MSP_OK;
+}
+
+// The lists of the instances idx[k] of a batch (all of one (m, n)), built
+// together: the host part per instance, then one upload per array kind and,
+// per side, one count launch, one offsets launch (one block per instance)
+// and one placement launch over the inner quarters of all instances.
+int build_direct_lists_batch(const int32_t *const *A, const int32_t *const *d, const std::vector<int> &idx, int m,
+                             int n, const DirectPlan &dp, const Plan &kp, DevAlloc &da, Copier &cp, Prof &prof,
+                             std::vector<DirectLists> &lists) {
+  cudaStream_t s = cp.s;
+  const size_t K = idx.size();
+  const uint32_t M = 1u << dp.B;
+  lists.assign(K, DirectLists{});
+  std::vector<InnerSeg> segs(2 * K);  // segment side * K + k
+  std::vector<uint64_t> icol_h[2];
+  std::vector<uint32_t> ok_h[2], oc_h[2], om_h[2];
+  std::vector<uint64_t> ov_h[2];
+  for (size_t k = 0; k < K; ++k) {
+    InnerGen g[2];
+    std::vector<uint64_t> icol[2];
+    prep_direct_host(A[idx[k]], d[idx[k]], m, n, dp, kp, lists[k], g, icol);
+    for (int sd = 0; sd < 2; ++sd) {
+      segs[sd * K + k].g = g[sd];
+      icol_h[sd].insert(icol_h[sd].end(), icol[sd].begin(), icol[sd].end());
+      ok_h[sd].insert(ok_h[sd].end(), lists[k].okey[sd].begin(), lists[k].okey[sd].end());
+      oc_h[sd].insert(oc_h[sd].end(), lists[k].ocls[sd].begin(), lists[k].ocls[sd].end());
+      om_h[sd].insert(om_h[sd].end(), lists[k].omask[sd].begin(), lists[k].omask[sd].end());
+      ov_h[sd].insert(ov_h[sd].end(), lists[k].ovec[sd].begin(), lists[k].ovec[sd].end());
+    }
+  }
+  for (int sd = 0; sd < 2; ++sd) {
+    const uint64_t ni = uint64_t(1) << dp.qi[sd];
+    const size_t no = size_t(1) << dp.qo[sd];
+    const size_t nic = icol_h[sd].size() / K;
+    uint32_t *ikey, *imask, *ioff, *cnt, *okey, *ocls, *omask;
+    uint64_t *icol, *ovec;
+    CK(da.get(&ikey, ni * K));
+    CK(da.get(&imask, ni * K));
+    CK(da.get(&ioff, ((size_t)M + 1) * K));
+    CK(da.get(&cnt, (size_t)M * K));
+    CK(da.get(&icol, icol_h[sd].size()));
+    CK(da.get(&okey, no * K));
+    CK(da.get(&ocls, no * K));
+    CK(da.get(&omask, no * K));
+    CK(da.get(&ovec, 4 * no * K));
+    CK(cp.h2d(icol, icol_h[sd].data(), 8 * icol_h[sd].size()));
+    CK(cp.h2d(okey, ok_h[sd].data(), 4 * no * K));
+    CK(cp.h2d(ocls, oc_h[sd].data(), 4 * no * K));
+    CK(cp.h2d(omask, om_h[sd].data(), 4 * no * K));
+    CK(cp.h2d(ovec, ov_h[sd].data(), 32 * no * K));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * M * K, s));
+    for (size_t k = 0; k < K; ++k) {
+      DirectLists &L = lists[k];
+      L.ikey[sd] = ikey + ni * k;
+      L.imask[sd] = imask + ni * k;
+      L.ioff[sd] = ioff + ((size_t)M + 1) * k;
+      L.icol[sd] = icol + nic * k;
+      L.d_okey[sd] = okey + no * k;
+      L.d_ocls[sd] = ocls + no * k;
+      L.d_omask[sd] = omask + no * k;
+      L.d_ovec[sd] = ovec + 4 * no * k;
+      InnerSeg &S = segs[sd * K + k];
+      S.cnt = cnt + (size_t)M * k;
+      S.ioff = L.ioff[sd];
+      S.ikey = L.ikey[sd];
+      S.imask = L.imask[sd];
+    }
+  }
+  InnerSeg *d_segs;
+  CK(da.get(&d_segs, 2 * K));
+  CK(cp.h2d(d_segs, segs.data(), sizeof(InnerSeg) * 2 * K));
+  for (int pass = 0; pass < 2; ++pass) {  // 0: counts, 1: placement
+    if (pass == 1) {
+      if (M <= (1u << 20)) {
+        LAUNCH(MSP_K_BUCKET, 1, 0,
+               (direct_inner_offsets_kernel<<<static_cast<unsigned>(2 * K), 1024, 0, s>>>(d_segs, M),
+                cudaGetLastError()));
+      } else {
+        uint32_t *scantmp;
+        CK(da.get(&scantmp, ((size_t)M + 1 + 4095) / 4096 + 1));
+        for (size_t i = 0; i < 2 * K; ++i) {
+          LAUNCH(MSP_K_BUCKET, 3, 0, launch_scan_u32(segs[i].cnt, segs[i].ioff, M, scantmp, s));
+          CK(cudaMemcpyAsync(segs[i].cnt, segs[i].ioff, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, s));
+        }
+      }
+    }
+    for (int sd = 0; sd < 2; ++sd) {
+      const int q = dp.qi[sd];
+      const int c = std::min(q, kGenChunk);
+      const uint64_t per = (uint64_t(1) << q) >> c;
+      const uint64_t total = per * K;
+      const unsigned blocks = static_cast<unsigned>(std::min<uint64_t>((total + 255) / 256, 1u << 20));
+      const InnerSeg *sp = d_segs + sd * K;
+      if (pass == 0)
+        LAUNCH(MSP_K_BUCKET, 1, 0,
+               (direct_inner_batch_kernel<false><<<blocks, 256, 0, s>>>(sp, c, per, total), cudaGetLastError()));
+      else
+        LAUNCH(MSP_K_BUCKET, 1, 0,
+               (direct_inner_batch_kernel<true><<<blocks, 256, 0, s>>>(sp, c, per, total), cudaGetLastError()));
+    }
   }
   return MSP_OK;
 }
@@ -1168,7 +1358,7 @@ int solve_batch_direct(const int32_t *const *A, const int32_t *const *d, int m, 
   // must fit the budget
   if ((uint64_t)K << dp.B > (1ull << 32)) return kDirectFallback;
   const double per_inst = 8.0 * (std::ldexp(1.0, dp.qi[0]) + std::ldexp(1.0, dp.qi[1])) +
-                          8.0 * (std::ldexp(1.0, dp.B) + 1) + (64 << 10);
+                          16.0 * (std::ldexp(1.0, dp.B) + 1) + (64 << 10);
   if (per_inst * K + (double)direct_footprint(dp) > (double)budget) return kDirectFallback;
 
   DevAlloc da(s);
@@ -1177,12 +1367,9 @@ int solve_batch_direct(const int32_t *const *A, const int32_t *const *d, int m, 
   Prof prof;
   prof.s = s;
   prof.st = &scratch;
-  std::vector<DirectLists> lists(K);
-  uint32_t *cnt, *scantmp;
-  CK(da.get(&cnt, (size_t)M + 1));
-  CK(da.get(&scantmp, ((size_t)M + 1 + 4095) / 4096 + 1));
-  for (uint32_t k = 0; k < K; ++k) {
-    const int rc = build_direct_lists(A[idx[k]], d[idx[k]], m, n, dp, kp, da, cp, prof, cnt, scantmp, lists[k]);
+  std::vector<DirectLists> lists;
+  {
+    const int rc = build_direct_lists_batch(A, d, idx, m, n, dp, kp, da, cp, prof, lists);
     if (rc != MSP_OK) return rc;
   }
   std::vector<std::vector<uint64_t>> out;
