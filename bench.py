@@ -49,8 +49,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--m", type=int, default=M_)
-    ap.add_argument("--n", type=int, default=N_)
+    # --rows / --cols (--m / --n also work when bench.py is run directly;
+    # torch.distributed.run would read those two as abbreviations of its own)
+    ap.add_argument("--rows", "--m", dest="m", type=int, default=M_)
+    ap.add_argument("--cols", "--n", dest="n", type=int, default=N_)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", choices=["9_80", "batch_6_50", "serving", "10_90_part", "profile_part",
                                          "profile_small"],
