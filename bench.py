@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--cols", "--n", dest="n", type=int, default=N_)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", choices=["9_80", "batch_6_50", "serving", "10_90_part", "profile_part",
-                                         "profile_small"],
+                                         "profile_small", "first_9_80"],
                     default="9_80",
                     help="9_80 (default): the headline exhaustive solve; batch_6_50: 64 (6,50) "
                          "instances in one batched call vs one at a time; serving: the mixed Poisson "
@@ -64,10 +64,12 @@ def parse():
                          "the case the ncu traffic captures use (the (9,80) instance of the default "
                          "workload over 1/4096 of its residue classes, one solve); profile_small: one "
                          "direct-pass solve of a (7,60) instance (lists of 8 MB), the case of the "
-                         "full-section captures")
+                         "full-section captures; first_9_80: time to the first solution (the "
+                         "quantity of the paper's tables) of the plain bench instance and of a "
+                         "planted (9,80) instance")
     ap.add_argument("--path", type=int, default=1, choices=[0, 1],
                     help="profile_part: 1 = direct pass, 0 = streaming pass")
-    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--rate-factor", type=float, default=0.8)
     return ap.parse_args()
 
@@ -584,6 +586,37 @@ def bench_profile_small(args):
            "solutions": len(sols), "records_done": st["records_done"], "kernels": st["kernels"]})
 
 
+def bench_first(args):
+    """Time to the first solution (the paper's Algorithm 2 returns the first
+    x; its Table 1 times are most likely time to first), on the direct pass:
+    the plain bench instance (7 solutions) and a planted one."""
+    import paper_2507_05045_gb300 as msp
+    from paper_2507_05045_gb300 import build
+    build.build()
+    rows = []
+    for name, (A, d, _) in (("plain seed 9080", mi.generate(M_, N_, SEED)),
+                            ("planted seed 9 (40 ones)", mi.generate(M_, N_, 9, planted=True, h=40))):
+        with msp.Instance(A, d, first=True) as inst:
+            for _ in range(args.warmup):
+                inst.solve_all()
+            ts = []
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                sols = inst.solve_all()
+                ts.append(time.perf_counter() - t0)
+            st = inst.stats()
+        rows.append({"instance": f"({M_},{N_}) {name}", "time_to_first_s": float(np.mean(ts)),
+                     "solutions_found": len(sols), "classes_done": st["classes_done"],
+                     "classes_total": st["classes_total"]})
+    _emit({"metric": "time to first solution at (9,80)", "value": rows[0]["time_to_first_s"], "unit": "s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+           "dtype": "u32", "data": "synthetic",
+           "config": {"workload": "(9,80) plain seed 9080 and planted seed 9, direct pass, stop after the "
+                                  "first launch (about 2^32 records) that yields a solution"},
+           "instances": rows,
+           "paper": "236.07 s average over four QOBLIB (9,80,100) instances, hybrid CPU+H200 (Table 1)"})
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_init(args)
@@ -605,6 +638,9 @@ def main():
         elif args.config == "profile_small":
             if rank == 0:
                 bench_profile_small(args)
+        elif args.config == "first_9_80":
+            if rank == 0:
+                bench_first(args)
         else:
             native(args, world, rank, local, pg)
     finally:

@@ -167,7 +167,18 @@ MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
  *                        of the three streaming-pass options is set.
  *   MSP_OPT_TABLE_BITS   shared hash table of the direct pass: 2^value slots,
  *                        value in [12, 15]; -1 = 14.
- *                        Either choice gives the same solutions. */
+ *                        Either choice gives the same solutions.
+ *   MSP_OPT_FIRST        1 = time to first solution (the quantity the paper's
+ *                        Algorithm 2 returns): on the direct pass the residue
+ *                        classes are joined in launches of about 2^32
+ *                        records, the matches verified after each, and the
+ *                        solve stops after the first launch that yields a
+ *                        solution.  The result is then a nonempty subset of
+ *                        the solutions (all of those found so far) and
+ *                        msp_stats.classes_done counts the classes joined;
+ *                        an instance with no solution is still searched to
+ *                        the end.  0 = every solution (default).  The
+ *                        streaming and exact passes ignore it. */
 enum {
   MSP_OPT_EXACT_PATH = 1,
   MSP_OPT_CLASS_PART = 2,
@@ -176,7 +187,8 @@ enum {
   MSP_OPT_DIGIT_BITS = 5,
   MSP_OPT_INNER_BITS = 6,
   MSP_OPT_DIRECT = 7,
-  MSP_OPT_TABLE_BITS = 8
+  MSP_OPT_TABLE_BITS = 8,
+  MSP_OPT_FIRST = 9
 };
 MSP_API int msp_set_option(msp_instance *inst, int option, int64_t value);
 

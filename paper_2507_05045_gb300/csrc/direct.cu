@@ -282,11 +282,13 @@ int build_direct_lists_batch(const int32_t *const *A, const int32_t *const *d, c
 // The class joins and the verification of the instances `lists` (all of one
 // (m, n)), over the residue classes [c_begin, c_end) of each.  Solutions go
 // to out[instance] as two words each (unsorted); st (may be null) receives
-// passes, records, matches and pairs verified.  Returns MSP_OK,
-// kDirectFallback, or an error status.
+// passes, records, matches and pairs verified.  With `first`, the matches
+// are verified after every launch and the classes stop after the first
+// launch that yields a solution (*classes_done: classes joined).  Returns
+// MSP_OK, kDirectFallback, or an error status.
 int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint32_t c_begin, uint32_t c_end,
-               DevAlloc &da, Copier &cp, Prof &prof, msp_stats *st, const volatile int *cancel,
-               std::vector<std::vector<uint64_t>> &out) {
+               DevAlloc &da, Copier &cp, Prof &prof, msp_stats *st, const volatile int *cancel, bool first,
+               uint32_t *classes_done, std::vector<std::vector<uint64_t>> &out) {
   cudaStream_t s = cp.s;
   const uint32_t M = 1u << dp.B, cmask = M - 1u;
   const uint32_t K = static_cast<uint32_t>(lists.size());
@@ -356,7 +358,72 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
   CK(da.get(&work, nlaunch));
   CK(cudaMemsetAsync(work, 0, sizeof(unsigned int) * nlaunch, s));
   const double per_class_in = 4.0 * (p.no[0] + p.no[1]);
+
+  // ---- verification of the matches [m0, m1) (one block each) ----
+  DirectVerify v{};
+  v.inst = d_vtab;
+  for (int sd = 0; sd < 2; ++sd) {
+    v.qi[sd] = dp.qi[sd];
+    v.col_o[sd] = dp.col_o[sd];
+    v.col_i[sd] = dp.col_i[sd];
+  }
+  v.W = dp.W;
+  v.class_bits = static_cast<uint32_t>(dp.B);
+  v.cmask = cmask;
+  unsigned long long *cnts;
+  unsigned int *ovf;
+  CK(da.get(&cnts, 2));
+  CK(da.get(&ovf, 1));
+  v.sol_count = cnts;
+  v.pairs = cnts + 1;
+  v.overflow = ovf;
+  uint64_t pairs_verified = 0, nsol = 0;
+  auto verify = [&](uint64_t m0, uint64_t m1) -> int {
+    if (m1 <= m0) return MSP_OK;
+    v.match_key = match_key + m0;
+    v.match_cls = match_cls + m0;
+    uint64_t cap = 1u << 16;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      uint64_t *sol;
+      CK(da.get(&sol, 3 * cap));
+      v.sol = sol;
+      v.sol_cap = cap;
+      CK(cudaMemsetAsync(cnts, 0, 2 * sizeof(unsigned long long), s));
+      CK(cudaMemsetAsync(ovf, 0, sizeof(unsigned int), s));
+      LAUNCH(MSP_K_VERIFY, 1, 0, launch_direct_verify(v, static_cast<unsigned>(m1 - m0), s));
+      unsigned long long hc[2];
+      unsigned int ovf_h = 0;
+      CK(cp.d2h(hc, cnts, sizeof(hc)));
+      CK(cp.d2h(&ovf_h, ovf, sizeof(ovf_h)));
+      CK(cudaStreamSynchronize(s));
+      if (ovf_h) return kDirectFallback;
+      if (hc[0] <= cap) {
+        pairs_verified += hc[1];
+        nsol += hc[0];
+        std::vector<uint64_t> h(3 * hc[0]);
+        if (hc[0]) {
+          CK(cp.d2h(h.data(), sol, sizeof(uint64_t) * 3 * hc[0]));
+          CK(cudaStreamSynchronize(s));
+        }
+        da.free1(sol, sizeof(uint64_t) * 3 * cap);
+        for (uint64_t i = 0; i < hc[0]; ++i) {
+          const uint64_t k = h[3 * i + 2];
+          if (k >= K) return fail(MSP_ECUDA, "verification produced an invalid instance tag");
+          out[k].push_back(h[3 * i]);
+          out[k].push_back(h[3 * i + 1]);
+        }
+        return MSP_OK;
+      }
+      da.free1(sol, sizeof(uint64_t) * 3 * cap);
+      if (hc[0] > (1ull << 28)) return fail(MSP_EOVERFLOW, "more than 2^28 solutions");
+      cap = hc[0];
+    }
+    return MSP_OK;
+  };
+
   int passes = 0;
+  uint64_t verified_to = 0;  // first-solution mode: matches verified so far
+  uint32_t classes_run = 0;
   for (uint32_t li = 0; li < nlaunch; ++li) {
     if (cancel && *cancel) return fail(MSP_ECANCELED, "request canceled");
     p.c0 = c_begin + li * per_launch;
@@ -369,7 +436,22 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
     LAUNCH(MSP_K_DIRECT, 1, static_cast<uint64_t>(4.0 * rec_est + per_class_in * p.nclass * K),
            launch_direct_join(dp.TB, p, s));
     ++passes;
+    classes_run += p.nclass;
+    if (first) {
+      // stop after the launch whose matches verify to a solution
+      unsigned long long nm = 0;
+      CK(cp.d2h(&nm, match_count, sizeof(nm)));
+      CK(cudaStreamSynchronize(s));
+      if (nm > kDirectMatchCap) break;
+      if (nm > verified_to) {
+        const int rc = verify(verified_to, nm);
+        if (rc != MSP_OK) return rc;
+        verified_to = nm;
+        if (nsol) break;
+      }
+    }
   }
+  if (classes_done) *classes_done = classes_run;
   unsigned long long nmatch = 0, nrec = 0;
   unsigned int err_h = 0;
   CK(cp.d2h(&nmatch, match_count, sizeof(nmatch)));
@@ -384,60 +466,11 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
     if (prof.on) st->kernel_bytes[MSP_K_DIRECT] = 4 * nrec + static_cast<uint64_t>(per_class_in * ncls * K);
   }
   if (err_h || nmatch > kDirectMatchCap) return kDirectFallback;
-  if (nmatch == 0) return MSP_OK;
-
-  DirectVerify v{};
-  v.inst = d_vtab;
-  for (int sd = 0; sd < 2; ++sd) {
-    v.qi[sd] = dp.qi[sd];
-    v.col_o[sd] = dp.col_o[sd];
-    v.col_i[sd] = dp.col_i[sd];
+  if (!first || nsol == 0) {
+    const int rc = verify(verified_to, nmatch);
+    if (rc != MSP_OK) return rc;
   }
-  v.W = dp.W;
-  v.class_bits = static_cast<uint32_t>(dp.B);
-  v.cmask = cmask;
-  v.match_key = match_key;
-  v.match_cls = match_cls;
-  unsigned long long *cnts;
-  unsigned int *ovf;
-  CK(da.get(&cnts, 2));
-  CK(da.get(&ovf, 1));
-  v.sol_count = cnts;
-  v.pairs = cnts + 1;
-  v.overflow = ovf;
-  uint64_t cap = 1u << 16;
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    uint64_t *sol;
-    CK(da.get(&sol, 3 * cap));
-    v.sol = sol;
-    v.sol_cap = cap;
-    CK(cudaMemsetAsync(cnts, 0, 2 * sizeof(unsigned long long), s));
-    CK(cudaMemsetAsync(ovf, 0, sizeof(unsigned int), s));
-    LAUNCH(MSP_K_VERIFY, 1, 0, launch_direct_verify(v, static_cast<unsigned>(nmatch), s));
-    unsigned long long hc[2];
-    unsigned int ovf_h = 0;
-    CK(cp.d2h(hc, cnts, sizeof(hc)));
-    CK(cp.d2h(&ovf_h, ovf, sizeof(ovf_h)));
-    CK(cudaStreamSynchronize(s));
-    if (ovf_h) return kDirectFallback;
-    if (st) st->pairs_verified = hc[1];
-    if (hc[0] <= cap) {
-      std::vector<uint64_t> h(3 * hc[0]);
-      if (hc[0]) {
-        CK(cp.d2h(h.data(), sol, sizeof(uint64_t) * 3 * hc[0]));
-        CK(cudaStreamSynchronize(s));
-      }
-      for (uint64_t i = 0; i < hc[0]; ++i) {
-        const uint64_t k = h[3 * i + 2];
-        if (k >= K) return fail(MSP_ECUDA, "verification produced an invalid instance tag");
-        out[k].push_back(h[3 * i]);
-        out[k].push_back(h[3 * i + 1]);
-      }
-      break;
-    }
-    if (hc[0] > (1ull << 28)) return fail(MSP_EOVERFLOW, "more than 2^28 solutions");
-    cap = hc[0];
-  }
+  if (st) st->pairs_verified = pairs_verified;
   return MSP_OK;
 }
 
@@ -500,7 +533,10 @@ int solve_direct(msp_instance *inst, const DirectPlan &dp, const Plan &kp, size_
   st.classes_total = M;
   st.classes_done = c_end - c_begin;
   std::vector<std::vector<uint64_t>> out;
-  const int rc = run_direct(lists, dp, c_begin, c_end, da, cp, prof, &st, inst->cancel, out);
+  uint32_t done = 0;
+  const int rc =
+      run_direct(lists, dp, c_begin, c_end, da, cp, prof, &st, inst->cancel, inst->first_only, &done, out);
+  st.classes_done = done;
   if (rc != MSP_OK) return rc;
   res = std::move(out[0]);
   st.device_bytes = da.peak;
@@ -553,7 +589,7 @@ int solve_batch_direct(const int32_t *const *A, const int32_t *const *d, int m, 
     if (rc != MSP_OK) return rc;
   }
   std::vector<std::vector<uint64_t>> out;
-  const int rc = run_direct(lists, dp, 0, M, da, cp, prof, nullptr, nullptr, out);
+  const int rc = run_direct(lists, dp, 0, M, da, cp, prof, nullptr, nullptr, false, nullptr, out);
   if (rc != MSP_OK) return rc;
   for (uint32_t k = 0; k < K; ++k) raw[idx[k]] = std::move(out[k]);
   da.release();

@@ -26,6 +26,7 @@ struct msp_instance {
   int plan_B = -1, plan_D = -1, plan_inner = -1;  // plan overrides (-1 = formula)
   int direct = -1;      // direct pass: -1 auto, 0 never, 1 whenever the instance fits it
   int table_bits = -1;  // direct pass shared-table bits (-1 = default)
+  bool first_only = false;  // direct pass: stop once a solution is found
 };
 
 namespace msp {

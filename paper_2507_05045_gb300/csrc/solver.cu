@@ -895,6 +895,10 @@ int msp_set_option(msp_instance *inst, int option, int64_t value) {
       if (value < -1 || value > 1) return fail(MSP_ERANGE, "direct must be -1, 0 or 1");
       inst->direct = static_cast<int>(value);
       return MSP_OK;
+    case MSP_OPT_FIRST:
+      if (value < 0 || value > 1) return fail(MSP_ERANGE, "first must be 0 or 1");
+      inst->first_only = value != 0;
+      return MSP_OK;
     case MSP_OPT_TABLE_BITS:
       if (value != -1 && (value < 12 || value > 15)) return fail(MSP_ERANGE, "table bits must be -1 or lie in [12, 15]");
       inst->table_bits = static_cast<int>(value);

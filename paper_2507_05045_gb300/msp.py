@@ -31,7 +31,7 @@ EXPORTED_SYMBOLS = (
 # msp_set_option codes (include/msp.h)
 OPT_EXACT_PATH, OPT_CLASS_PART, OPT_CLASS_PARTS = 1, 2, 3
 OPT_CLASS_BITS, OPT_DIGIT_BITS, OPT_INNER_BITS = 4, 5, 6
-OPT_DIRECT, OPT_TABLE_BITS = 7, 8
+OPT_DIRECT, OPT_TABLE_BITS, OPT_FIRST = 7, 8, 9
 PLAN_KEYS = {"class_bits": OPT_CLASS_BITS, "digit_bits": OPT_DIGIT_BITS, "inner_bits": OPT_INNER_BITS,
              "direct": OPT_DIRECT, "table_bits": OPT_TABLE_BITS}
 
@@ -153,12 +153,14 @@ class Instance:
     """One (A, d) instance: ``msp_create`` / ``msp_solve_all`` / ``msp_destroy``."""
 
     def __init__(self, A, d, stream: int | None = None, memory_budget: int = 0, profiling: bool = False,
-                 exact_path: bool = False, class_part: tuple[int, int] | None = None, plan=None):
+                 exact_path: bool = False, class_part: tuple[int, int] | None = None, plan=None,
+                 first: bool = False):
         """``plan``: None (built-in formulas), a dict with any of ``class_bits``,
         ``digit_bits``, ``inner_bits`` (streaming pass), ``direct`` (-1, 0, 1)
         and ``table_bits`` (direct pass; see MSP_OPT_* in msp.h), or
         ``"auto"`` for the autotuner's cached choice for this device and
-        (m, n), if any."""
+        (m, n), if any.  ``first``: stop once a solution is found (direct
+        pass; MSP_OPT_FIRST)."""
         lib = load_library()
         A = np.asarray(A)
         if A.ndim != 2:
@@ -180,6 +182,8 @@ class Instance:
             _check(lib.msp_set_profiling(h, 1))
         if exact_path:
             _check(lib.msp_set_option(h, 1, 1))
+        if first:
+            _check(lib.msp_set_option(h, OPT_FIRST, 1))
         if class_part is not None:
             _check(lib.msp_set_option(h, OPT_CLASS_PARTS, int(class_part[1])))
             _check(lib.msp_set_option(h, OPT_CLASS_PART, int(class_part[0])))

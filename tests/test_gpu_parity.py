@@ -407,6 +407,32 @@ def test_streaming_pass_with_large_inner_quarters(msp):
     _check_solutions_exact(A, d, got)
 
 
+def test_first_solution_mode(msp):
+    # time-to-first: a nonempty subset of the full solution set, found before
+    # all classes are joined; an instance without solutions is searched to
+    # the end and returns none
+    A, d, x = mi.generate(8, 70, 8, planted=True, h=35)
+    full, st_full = solve(msp, A, d, {"direct": 1})
+    with msp.Instance(A, d, plan={"direct": 1}, first=True) as inst:
+        got = inst.solve_all()
+        st = inst.stats()
+    assert got and set(got) <= set(full)
+    _check_solutions_exact(A, d, got)
+    assert st["path"] == "direct"
+    assert 0 < st["classes_done"] <= st["classes_total"] == st_full["classes_total"]
+    assert st["records_done"] <= st_full["records_done"]
+    for seed in range(3):
+        A, d, _ = mi.generate(6, 50, 1000 + seed)
+        want = solve(msp, A, d, {"direct": 1})[0]
+        with msp.Instance(A, d, plan={"direct": 1}, first=True) as inst:
+            got = inst.solve_all()
+            st = inst.stats()
+        if not want:
+            assert got == [] and st["classes_done"] == st["classes_total"]
+        else:
+            assert got and set(got) <= set(want)
+
+
 def test_plan_options_are_validated(msp):
     A, d, _ = mi.generate(4, 30, 1)
     for bad in [{"class_bits": 24}, {"digit_bits": 13}, {"inner_bits": -2}, {"table_bits": 16},
