@@ -7,14 +7,17 @@
  * (Kempke and Koch, "A GPU accelerated variant of Schroeppel-Shamir's
  * algorithm for solving the market split problem", Section 1, eq. 1.)
  *
- * The columns are split into four quarters; every subset sum of each
- * quarter is generated by Gray code with all m row sums packed (Algorithm 1,
- * Section 2).  The key space of the left and right half-pairs is split into
- * residue classes of row 1 (and, for large n, a surrogate combination of the
- * first rows, eq. 2) so that each pass fits in device memory; inside a pass
- * the half-pair keys are radix-partitioned, sorted in shared memory and
- * merge-joined, and every key match is verified exactly on all m rows
- * (Algorithm 2 with the validation of Algorithm 3 and Section 3).
+ * The columns are split into four quarters whose subset sums are enumerated
+ * (Algorithm 1, Section 2).  The key space of the left and right half-pairs
+ * is split into residue classes of row 1 or of a surrogate combination of
+ * the first rows (eq. 2); only half-pairs of one class can match.  On the
+ * direct pass (every instance whose halves have at most 40 columns) a class
+ * holds about 2^13 half-pairs per side and one thread block joins it in
+ * shared memory; larger instances take the streaming pass, which
+ * radix-partitions the half-pairs of a batch of classes through device
+ * memory and joins each partition in shared memory.  Every key match is
+ * verified exactly on all m rows (Algorithm 2 with the validation of
+ * Algorithm 3 and Section 3).
  *
  * Conventions for every entry point:
  *   - All pointers are HOST pointers unless a name says otherwise.  Inputs

@@ -4,7 +4,7 @@
 //
 // Split.  The columns are cut into a left half (L, the first ceil(n/2)) and a
 // right half (R).  Each half is split again into an OUTER quarter of at most
-// 2^10 subsets and an INNER quarter of up to 2^31 subsets: the four lists of
+// 2^9 subsets and an INNER quarter of up to 2^31 subsets: the four lists of
 // Algorithm 1 (Section 2) with very uneven sizes, which leaves |L| and |R|,
 // and so the work, unchanged.
 //
@@ -25,12 +25,15 @@
 //
 //   direct_inner_count/scatter_kernel  build the bucketed inner lists
 //                       (counting sort of all 2^qi subsets by class; each
-//                       thread walks a chunk of subsets in Gray order).
+//                       thread walks a chunk of subsets in Gray order);
+//                       direct_inner_batch/offsets_kernel do the same for
+//                       every instance of a batch at once.
 //   direct_join_kernel  persistent blocks take runs of consecutive classes
-//                       from a work counter; per class the L keys are
-//                       inserted into a shared open-addressing table, then
-//                       the R keys probe it; a matched (class, key) is
-//                       appended to a device list.
+//                       (of any instance) from a work counter; per class
+//                       the L keys set a shared filter and fill buckets of a
+//                       shared table, then the R keys test the filter and
+//                       the few that pass look up the table; a matched
+//                       (class, key) is appended to a device list.
 //   direct_verify_kernel one block per matched (class, key): finds every
 //                       L pair (a, b) and R pair (c, e) with that key by
 //                       scanning the class's inner buckets, and checks each
@@ -215,13 +218,11 @@ __device__ __forceinline__ void emit_match(const DirectPass &p, bool e, uint32_t
 // lies in [lo, hi) is handed to f(okm, key) in batches of kBatch records per
 // lane: key[b] is the join key of record i0 + 32 b + lane, bit b of okm says
 // whether that record exists.  f is called by all lanes of the warp.  The
-// inner keys of the next batch are loaded before f runs on the current one,
-// so their latency overlaps the table work.
+// inner keys of a batch are loaded together, so their latencies overlap.
 // Record k belongs to the last nonempty subset whose first record is <= k;
 // a bitmap marks the first records (1024 records per segment, one word per
 // lane) and a compacted per-warp table holds (start - first record, ka).
 constexpr int kBatch = 4;
-constexpr bool kPipe = false;  // load the next batch before working on this one
 
 template <typename F>
 __device__ __forceinline__ void group_records(uint32_t st, uint32_t len, uint32_t ka,
@@ -280,31 +281,12 @@ __device__ __forceinline__ void group_records(uint32_t st, uint32_t len, uint32_
         okm |= static_cast<uint32_t>(ok) << b;
       }
     };
-    uint32_t rc[kBatch], kc[kBatch], okc;
-    if constexpr (kPipe) fetch(S, rc, kc, okc);
     for (uint32_t i0 = S; i0 < send; i0 += 32u * kBatch) {
-      uint32_t key[kBatch];
-      if constexpr (kPipe) {
-        uint32_t rn[kBatch], kn[kBatch], okn = 0u;
-        const bool more = i0 + 32u * kBatch < send;  // warp-uniform
-        if (more) fetch(i0 + 32u * kBatch, rn, kn, okn);
+      uint32_t rc[kBatch], kc[kBatch], okc, key[kBatch];
+      fetch(i0, rc, kc, okc);
 #pragma unroll
-        for (int b = 0; b < kBatch; ++b) key[b] = kc[b] + rc[b];
-        f(okc, key);
-        if (more) {
-#pragma unroll
-          for (int b = 0; b < kBatch; ++b) {
-            rc[b] = rn[b];
-            kc[b] = kn[b];
-          }
-          okc = okn;
-        }
-      } else {
-        fetch(i0, rc, kc, okc);
-#pragma unroll
-        for (int b = 0; b < kBatch; ++b) key[b] = kc[b] + rc[b];
-        f(okc, key);
-      }
+      for (int b = 0; b < kBatch; ++b) key[b] = kc[b] + rc[b];
+      f(okc, key);
     }
   }
 }
