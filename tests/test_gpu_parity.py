@@ -84,6 +84,34 @@ def test_tiny_n_every_quarter_shape(msp, n, plan):
 
 
 @pytest.mark.parametrize("plan", PATHS)
+def test_sixteen_rows_and_wide_row_sums(msp, plan):
+    # m = 16: four packed 16-bit words per vector; row sums near the 2^16
+    # field limit with large coefficients
+    for seed in range(3):
+        A, d, _ = mi.generate(16, 20, 5 + seed, K=50, planted=True, h=10)
+        assert solve(msp, A, d, plan)[0] == oracle.brute(A, d)
+    A, d, _ = mi.generate(3, 21, 6, K=3100, planted=True, h=10)
+    assert A.sum(axis=1).max() > 30000
+    assert solve(msp, A, d, plan)[0] == oracle.brute(A, d)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_sweep_all_paths(msp, seed):
+    # random shapes and coefficient ranges: direct, streaming and exact passes
+    # against the oracle
+    rng = np.random.default_rng(seed)
+    m = int(rng.integers(1, 17))
+    n = int(rng.integers(10, 31))
+    K = int(rng.choice([2, 3, 7, 100, 1000]))
+    A, d, _ = mi.generate(m, n, 20000 + seed, K=K, planted=bool(seed % 2), h=n // 2)
+    want = oracle.brute(A, d) if n <= 20 else oracle.mitm(A, d)
+    assert solve(msp, A, d, {"direct": 1})[0] == want
+    assert solve(msp, A, d, {"direct": 0})[0] == want
+    with msp.Instance(A, d, exact_path=True) as inst:
+        assert inst.solve_all() == want
+
+
+@pytest.mark.parametrize("plan", PATHS)
 def test_degenerate_inputs(msp, plan):
     # all-zero matrix: every vector solves d = 0, none solves d != 0
     A = np.zeros((3, 12), np.int32)
