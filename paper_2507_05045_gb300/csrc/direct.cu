@@ -370,9 +370,9 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
   v.W = dp.W;
   v.class_bits = static_cast<uint32_t>(dp.B);
   v.cmask = cmask;
-  unsigned long long *cnts;
+  unsigned long long *cnts;  // solutions, then the pair counters
   unsigned int *ovf;
-  CK(da.get(&cnts, 2));
+  CK(da.get(&cnts, 1 + kVerifyPairSlots));
   CK(da.get(&ovf, 1));
   v.sol_count = cnts;
   v.pairs = cnts + 1;
@@ -388,15 +388,17 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
       CK(da.get(&sol, 3 * cap));
       v.sol = sol;
       v.sol_cap = cap;
-      CK(cudaMemsetAsync(cnts, 0, 2 * sizeof(unsigned long long), s));
+      CK(cudaMemsetAsync(cnts, 0, (1 + kVerifyPairSlots) * sizeof(unsigned long long), s));
       CK(cudaMemsetAsync(ovf, 0, sizeof(unsigned int), s));
       LAUNCH(MSP_K_VERIFY, 1, 0, launch_direct_verify(v, static_cast<unsigned>(m1 - m0), s));
-      unsigned long long hc[2];
+      unsigned long long hcs[1 + kVerifyPairSlots];
       unsigned int ovf_h = 0;
-      CK(cp.d2h(hc, cnts, sizeof(hc)));
+      CK(cp.d2h(hcs, cnts, sizeof(hcs)));
       CK(cp.d2h(&ovf_h, ovf, sizeof(ovf_h)));
       CK(cudaStreamSynchronize(s));
       if (ovf_h) return kDirectFallback;
+      unsigned long long hc[2] = {hcs[0], 0};
+      for (int k = 1; k <= kVerifyPairSlots; ++k) hc[1] += hcs[k];
       if (hc[0] <= cap) {
         pairs_verified += hc[1];
         nsol += hc[0];

@@ -1,6 +1,7 @@
-// Shared declarations of the direct pass (direct_kernels.cu: device code,
-// direct.cu: host side).  The direct pass joins residue classes of about
-// 2^13 records per side entirely in shared memory; see direct_kernels.cu.
+// Shared declarations of the direct pass (direct_join.cu: the class joins,
+// direct_kernels.cu: list builds, verification and C1, direct.cu: host
+// side).  The direct pass joins residue classes of about 2^13 records per
+// side entirely in shared memory; direct_kernels.cu describes the method.
 #pragma once
 
 #include <cstdint>
@@ -12,6 +13,7 @@ constexpr int kDirectThreads = 512;          // threads per join block
 constexpr int kOuterMax = kDirectThreads;    // outer subsets per side: one per thread of a join block
 constexpr int kInnerMax = 31;                // inner quarter columns (32-bit positions)
 constexpr int kGenChunk = 6;                 // Gray walk of 2^6 subsets per thread
+constexpr int kVerifyPairSlots = 256;        // counters of checked pairs in verification
 
 struct InnerGen {
   uint32_t ck[kInnerMax];  // 32-bit key of each column (row sums weighted by w_i)
@@ -86,7 +88,7 @@ struct DirectVerify {
   uint64_t *sol;             // [sol_cap][3]: mask low word, high word, instance
   unsigned long long *sol_count;
   uint64_t sol_cap;
-  unsigned long long *pairs;
+  unsigned long long *pairs; // [kVerifyPairSlots] candidate pairs checked (summed by the host)
   unsigned int *overflow;    // a match had more candidates than the block holds
 };
 
