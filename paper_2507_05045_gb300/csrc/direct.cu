@@ -53,6 +53,8 @@ size_t direct_footprint(const DirectPlan &d) {
   for (int s = 0; s < 2; ++s) b += 8.0 * std::ldexp(1.0, d.qi[s]);  // inner keys and masks
   b += 2.0 * 4.0 * (std::ldexp(1.0, d.B) + 1);                       // bucket offsets
   b += 4.0 * (std::ldexp(1.0, d.B) + 1);                             // counts / cursors while building
+  b += 16.0 * std::ldexp(1.0, std::max(d.qi[0], d.qi[1]) - kHighMax) + 4096;  // low subsets while building
+  b += 8.0 * (std::ldexp(1.0, d.B) + 1) + 8.0 * (1 << kHighMax);     // coarse buckets, high subsets
   b += 12.0 * kDirectMatchCap + (64 << 20);                          // matches, small tables, margin
   return static_cast<size_t>(b);
 }
@@ -150,9 +152,11 @@ void prep_direct_host(const int32_t *A, const int32_t *d, int m, int n, const Di
 }
 
 // S0 + S1 + S2 of one instance: host preparation, then the inner lists
-// bucketed by class on the device (count, offsets, scatter).  `cnt` and
-// `scantmp` are scratch of 2^B + 1 and (2^B + 1) / 4096 + 1 entries, shared
-// by successive calls.
+// bucketed by class on the device: the low subsets by coarse class and the
+// high subsets, then class counts by windows, bucket starts and placement
+// by windows.  `cnt` and `scantmp` are
+// scratch of 2^B + 1 and (2^B + 1) / 4096 + 1 entries, shared by successive
+// calls.
 int build_direct_lists(const int32_t *A, const int32_t *d, int m, int n, const DirectPlan &dp, const Plan &kp,
                        DevAlloc &da, Copier &cp, Prof &prof, uint32_t *cnt, uint32_t *scantmp, DirectLists &L) {
   cudaStream_t s = cp.s;
@@ -168,12 +172,49 @@ int build_direct_lists(const int32_t *A, const int32_t *d, int m, int n, const D
     CK(da.get(&L.ioff[sd], (size_t)M + 1));
     CK(da.get(&L.icol[sd], icol[sd].size()));
     CK(cp.h2d(L.icol[sd], icol[sd].data(), sizeof(uint64_t) * icol[sd].size()));
-    const InnerGen &g = gs[sd];
-    CK(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * M, s));
-    LAUNCH(MSP_K_BUCKET, 1, 0, launch_direct_inner(g, cnt, nullptr, nullptr, s));
+  }
+  for (int sd = 0; sd < 2; ++sd) {
+    const int q = dp.qi[sd];
+    WinBuild w{};
+    w.B = dp.B;
+    w.cmask = M - 1u;
+    w.hq = std::min(q, kHighMax);
+    w.h = q - w.hq;
+    w.logW = std::min(kWinBits, dp.B);
+    w.gshift = std::max(0, w.logW - 2);
+    w.nc = 1u << (dp.B - w.gshift);
+    const size_t nl = size_t(1) << w.h;
+    uint4 *low;
+    uint32_t *lcur, *loff, *hkey, *hcls;
+    CK(da.get(&low, nl));
+    CK(da.get(&lcur, (size_t)w.nc + 1));
+    CK(da.get(&loff, (size_t)w.nc + 1));
+    CK(da.get(&hkey, size_t(1) << w.hq));
+    CK(da.get(&hcls, size_t(1) << w.hq));
+    InnerGen gl = gs[sd];
+    gl.q = w.h;
+    CK(cudaMemsetAsync(lcur, 0, sizeof(uint32_t) * w.nc, s));
+    LAUNCH(MSP_K_BUCKET, 1, 0, launch_win_low(gl, w.gshift, lcur, nullptr, s));
+    LAUNCH(MSP_K_BUCKET, 3, 0, launch_scan_u32(lcur, loff, w.nc, scantmp, s));
+    CK(cudaMemcpyAsync(lcur, loff, sizeof(uint32_t) * w.nc, cudaMemcpyDeviceToDevice, s));
+    LAUNCH(MSP_K_BUCKET, 1, 0, launch_win_low(gl, w.gshift, lcur, low, s));
+    LAUNCH(MSP_K_BUCKET, 1, 0, launch_win_high(gs[sd], w.h, w.hq, hkey, hcls, s));
+    w.low = low;
+    w.loff = loff;
+    w.hkey = hkey;
+    w.hcls = hcls;
+    w.cnt = cnt;
+    LAUNCH(MSP_K_BUCKET, 1, 0, launch_win(w, false, s));
     LAUNCH(MSP_K_BUCKET, 3, 0, launch_scan_u32(cnt, L.ioff[sd], M, scantmp, s));
-    CK(cudaMemcpyAsync(cnt, L.ioff[sd], sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, s));
-    LAUNCH(MSP_K_BUCKET, 1, 0, launch_direct_inner(g, cnt, L.ikey[sd], L.imask[sd], s));
+    w.ioff = L.ioff[sd];
+    w.ikey = L.ikey[sd];
+    w.imask = L.imask[sd];
+    LAUNCH(MSP_K_BUCKET, 1, 0, launch_win(w, true, s));
+    da.free1(hcls, sizeof(uint32_t) << w.hq);
+    da.free1(hkey, sizeof(uint32_t) << w.hq);
+    da.free1(loff, sizeof(uint32_t) * ((size_t)w.nc + 1));
+    da.free1(lcur, sizeof(uint32_t) * ((size_t)w.nc + 1));
+    da.free1(low, sizeof(uint4) * nl);
   }
   for (int sd = 0; sd < 2; ++sd) {
     const size_t no = L.okey[sd].size();

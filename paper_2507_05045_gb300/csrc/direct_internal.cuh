@@ -93,12 +93,34 @@ struct DirectVerify {
 };
 
 // Launchers (asynchronous on s; return cudaGetLastError()).
-// Counts the 2^q subsets of one inner quarter by class into cnt_or_cur
-// (ikey == nullptr), or places them at the cursors cnt_or_cur.
-cudaError_t launch_direct_inner(const InnerGen &g, uint32_t *cnt_or_cur, uint32_t *ikey, uint32_t *imask,
-                                cudaStream_t s);
-// The same for the inner quarters of every segment of a batch (all of q
-// columns): counts (scatter = false) or placement.
+// Inner list of one instance by windows of 2^logW classes: the q inner
+// columns split into h low and hq high ones; the low subsets, bucketed by
+// class at a granularity of 2^gshift classes, and the high subsets'
+// keys and classes are built first.
+constexpr int kWinBits = 9;            // classes per window (fewer when B < 9)
+constexpr int kHighMax = 10;           // high columns
+constexpr uint32_t kWinCap = 12288;    // subsets staged per window (mean 2^(q - B) per class)
+struct WinBuild {
+  int B;
+  uint32_t cmask;
+  int h, hq;                  // low and high columns
+  int logW, gshift;
+  uint32_t nc;                // coarse buckets, 2^(B - gshift)
+  const uint4 *low;           // [2^h] (key, mask, class, 0) by coarse bucket
+  const uint32_t *loff;       // [nc + 1] coarse bucket starts
+  const uint32_t *hkey, *hcls;  // [2^hq]
+  uint32_t *cnt;              // [2^B] class counts (first pass)
+  const uint32_t *ioff;       // [2^B + 1] bucket starts (second pass)
+  uint32_t *ikey, *imask;     // [2^q] the list (second pass)
+};
+// Low subsets (g.q = h) counted by coarse bucket (low == nullptr) or placed
+// at the cursors cnt_or_cur.
+cudaError_t launch_win_low(const InnerGen &g, int gshift, uint32_t *cnt_or_cur, uint4 *low, cudaStream_t s);
+cudaError_t launch_win_high(const InnerGen &g, int h, int hq, uint32_t *hkey, uint32_t *hcls, cudaStream_t s);
+// One block per window: class counts (place = false) or placement.
+cudaError_t launch_win(const WinBuild &w, bool place, cudaStream_t s);
+// Counts by class (scatter = false) or placement at the cursors of the
+// inner quarters of every segment of a batch (all of q columns).
 cudaError_t launch_direct_inner_batch(const InnerSeg *segs, int nseg, int q, bool scatter, cudaStream_t s);
 // Bucket starts of every segment of a batch (2^B <= 2^20): one block each.
 cudaError_t launch_direct_inner_offsets(const InnerSeg *segs, int nseg, uint32_t M, cudaStream_t s);

@@ -23,11 +23,12 @@
 // match is only a filter (like the hash encoding of Algorithm 4) and every
 // match is verified exactly on all m rows.
 //
-//   direct_inner_count/scatter_kernel  build the bucketed inner lists
-//                       (counting sort of all 2^qi subsets by class; each
-//                       thread walks a chunk of subsets in Gray order);
-//                       direct_inner_batch/offsets_kernel do the same for
-//                       every instance of a batch at once.
+//   win_low/high_kernel, win_kernel  build the bucketed inner list of one
+//                       instance: the low subsets (walked in Gray order) and
+//                       the high subsets of the quarter, then the list by
+//                       windows of classes, staged in shared memory;
+//                       direct_inner_batch/offsets_kernel build those of
+//                       every instance of a batch at once (one level).
 //   direct_join_kernel  (direct_join.cu) the class joins in shared memory.
 //   direct_verify_kernel one block per matched (class, key): finds every
 //                       L pair (a, b) and R pair (c, e) with that key by
@@ -76,25 +77,117 @@ __device__ __forceinline__ void walk_chunk(const InnerGen &g, uint32_t base, int
   }
 }
 
-__global__ void direct_inner_count_kernel(InnerGen g, int c, uint64_t nchunks, uint32_t *cnt) {
-  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nchunks;
-       t += (uint64_t)gridDim.x * blockDim.x) {
-    walk_chunk(g, static_cast<uint32_t>(t << c), c, [&](uint32_t, uint32_t, uint32_t r) { atomicAdd(cnt + r, 1u); });
-  }
-}
+// Inner list of one instance, built by windows of classes.  The q inner
+// columns split into h low and hq = min(q, 10) high ones.  The 2^h low
+// subsets are bucketed by class at a coarse granularity of 2^gshift classes
+// (a counting sort of at most 2^21 subsets).  Class r of the quarter holds
+// the pairs (H, l) with kappa(H) + kappa(l) = r, so for each high subset H
+// the classes of a window [w0, w0 + W) take the low subsets whose class
+// lies in the cyclic interval [w0 - kappa(H), w0 - kappa(H) + W): a few
+// coarse buckets, that is one contiguous run of the low list (two where the
+// interval wraps).  One block per window counts its classes (first pass);
+// given the bucket starts, it then places its subsets in a shared-memory
+// stage and writes the window's range of the list with coalesced stores
+// (second pass).  The random accesses all go to shared memory or to the low
+// list, which stays in L2.
+constexpr int kWinThreads = 512;
 
-__global__ void direct_inner_scatter_kernel(InnerGen g, int c, uint64_t nchunks, uint32_t *cur, uint32_t *ikey,
-                                            uint32_t *imask) {
+template <bool kScatter>
+__global__ void win_low_kernel(InnerGen g, int c, uint64_t nchunks, int gshift, uint32_t *cnt_or_cur, uint4 *low) {
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nchunks;
        t += (uint64_t)gridDim.x * blockDim.x) {
     walk_chunk(g, static_cast<uint32_t>(t << c), c, [&](uint32_t mask, uint32_t k, uint32_t r) {
-      const uint32_t pos = atomicAdd(cur + r, 1u);
-      ikey[pos] = k;
-      imask[pos] = mask;
+      if constexpr (kScatter) {
+        const uint32_t pos = atomicAdd(cnt_or_cur + (r >> gshift), 1u);
+        low[pos] = make_uint4(k, mask, r, 0u);
+      } else {
+        atomicAdd(cnt_or_cur + (r >> gshift), 1u);
+      }
     });
   }
 }
 
+// Key and class of every high subset H (columns h .. h + hq - 1).
+__global__ void win_high_kernel(InnerGen g, int h, int hq, uint32_t *hkey, uint32_t *hcls) {
+  const uint32_t H = blockIdx.x * blockDim.x + threadIdx.x;
+  if (H >= (1u << hq)) return;
+  uint32_t key = 0, cls = 0;
+  for (uint32_t b = H; b; b &= b - 1) {
+    const int j = h + __ffs(b) - 1;
+    key += g.ck[j];
+    cls += g.cc[j];
+  }
+  hkey[H] = g.neg ? 0u - key : key;
+  hcls[H] = (g.neg ? 0u - cls : cls) & g.cmask;
+}
+
+template <bool kPlace>
+__global__ void __launch_bounds__(kWinThreads) win_kernel(WinBuild w) {
+  extern __shared__ __align__(16) uint8_t wsm[];
+  uint2 *const stage = reinterpret_cast<uint2 *>(wsm);                  // [kWinCap] (place pass)
+  uint32_t *const cur = reinterpret_cast<uint32_t *>(wsm + (kPlace ? sizeof(uint2) * kWinCap : 0));  // [W]
+  const uint32_t W = 1u << w.logW;
+  const uint32_t w0 = blockIdx.x << w.logW;
+  uint32_t base = 0, total = 0;
+  if (kPlace) {
+    base = w.ioff[w0];
+    total = w.ioff[w0 + W] - base;
+  }
+  for (uint32_t i = threadIdx.x; i < W; i += kWinThreads) cur[i] = kPlace ? w.ioff[w0 + i] - base : 0u;
+  __syncthreads();
+  const bool staged = total <= kWinCap;
+  const bool whole = w.logW == w.B;  // one window: every low subset
+  const uint32_t nH = 1u << w.hq;
+  for (uint32_t H = threadIdx.x; H < nH; H += kWinThreads) {
+    const uint32_t kH = w.hkey[H], cH = w.hcls[H];
+    const uint32_t hm = H << w.h;
+    uint32_t a0, a1, b0 = 0, b1 = 0;  // runs [a0, a1) and [b0, b1) of the low list
+    if (whole) {
+      a0 = 0;
+      a1 = w.loff[w.nc];
+    } else {
+      const uint32_t st = (w0 - cH) & w.cmask;
+      const uint32_t en = (st + W - 1u) & w.cmask;
+      const uint32_t c1 = st >> w.gshift, c2 = en >> w.gshift;
+      a0 = w.loff[c1];
+      if (c2 >= c1) {
+        a1 = w.loff[c2 + 1];
+      } else {
+        a1 = w.loff[w.nc];
+        b1 = w.loff[c2 + 1];
+      }
+    }
+    auto visit = [&](uint32_t i) {
+      const uint4 e = w.low[i];
+      const uint32_t d = (cH + e.z - w0) & w.cmask;
+      if (d < W) {
+        const uint32_t pos = atomicAdd(cur + d, 1u);
+        if (kPlace) {
+          const uint32_t key = kH + e.x, mask = hm | e.y;
+          if (staged) {
+            stage[pos] = make_uint2(key, mask);
+          } else {
+            w.ikey[base + pos] = key;
+            w.imask[base + pos] = mask;
+          }
+        }
+      }
+    };
+#pragma unroll 4
+    for (uint32_t i = a0; i < a1; ++i) visit(i);
+    for (uint32_t i = b0; i < b1; ++i) visit(i);
+  }
+  __syncthreads();
+  if (!kPlace) {
+    for (uint32_t i = threadIdx.x; i < W; i += kWinThreads) w.cnt[w0 + i] = cur[i];
+  } else if (staged) {
+    for (uint32_t i = threadIdx.x; i < total; i += kWinThreads) {
+      const uint2 v = stage[i];
+      w.ikey[base + i] = v.x;
+      w.imask[base + i] = v.y;
+    }
+  }
+}
 
 // Counts (scatter = false) or bucket placement (scatter = true) of the inner
 // subsets of every segment of a batch: thread t walks chunk t mod
@@ -287,16 +380,41 @@ __global__ void __launch_bounds__(1024) c1_dp_kernel(const int32_t *a1, int n, i
 
 }  // namespace
 
-cudaError_t launch_direct_inner(const InnerGen &g, uint32_t *cnt_or_cur, uint32_t *ikey, uint32_t *imask,
-                                cudaStream_t s) {
+cudaError_t launch_win_low(const InnerGen &g, int gshift, uint32_t *cnt_or_cur, uint4 *low, cudaStream_t s) {
   const int c = g.q < kGenChunk ? g.q : kGenChunk;
   const uint64_t nchunks = (uint64_t(1) << g.q) >> c;
   const uint64_t want = (nchunks + 255) / 256;
   const unsigned blocks = static_cast<unsigned>(want < (1u << 20) ? want : (1u << 20));
-  if (ikey)
-    direct_inner_scatter_kernel<<<blocks, 256, 0, s>>>(g, c, nchunks, cnt_or_cur, ikey, imask);
+  if (low)
+    win_low_kernel<true><<<blocks, 256, 0, s>>>(g, c, nchunks, gshift, cnt_or_cur, low);
   else
-    direct_inner_count_kernel<<<blocks, 256, 0, s>>>(g, c, nchunks, cnt_or_cur);
+    win_low_kernel<false><<<blocks, 256, 0, s>>>(g, c, nchunks, gshift, cnt_or_cur, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_win_high(const InnerGen &g, int h, int hq, uint32_t *hkey, uint32_t *hcls, cudaStream_t s) {
+  const unsigned n = 1u << hq;
+  win_high_kernel<<<(n + 255) / 256, 256, 0, s>>>(g, h, hq, hkey, hcls);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_win(const WinBuild &w, bool place, cudaStream_t s) {
+  if (w.logW > w.B || w.B > 31 || w.h + w.hq > kInnerMax) return cudaErrorInvalidValue;
+  const unsigned windows = 1u << (w.B - w.logW);
+  const size_t cur = sizeof(uint32_t) << w.logW;
+  if (place) {
+    static bool attr = false;
+    const size_t smem = sizeof(uint2) * kWinCap + (sizeof(uint32_t) << kWinBits);
+    if (!attr) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(win_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    win_kernel<true><<<windows, kWinThreads, sizeof(uint2) * kWinCap + cur, s>>>(w);
+  } else {
+    win_kernel<false><<<windows, kWinThreads, cur, s>>>(w);
+  }
   return cudaGetLastError();
 }
 
