@@ -422,31 +422,21 @@ def test_direct_pass_on_skewed_classes(msp):
 
 
 def test_inner_list_window_past_the_stage(msp):
-    # n = 46 splits 23/23 with 2^10 classes and inner quarters of columns
-    # 9..22 and 32..45.  Zeroing the left inner quarter puts all of its 2^14
-    # subsets into one class, so their window of classes holds more subsets
-    # than the shared-memory stage and the list build places them directly.
-    # Each zero column doubles the solution set (every subset of the zero
-    # columns extends a solution of the other columns), which gives the
-    # expected set from the oracle on the 32 remaining columns.
+    # n = 46 splits 23/23 with 2^10 classes (keyed on rows 1-2) and inner
+    # quarters of columns 9..22 and 32..45.  With rows 1 and 2 zero on the
+    # left inner columns, all 2^14 left inner subsets fall into one class
+    # (their keys, set by rows 3-5, stay distinct), so its window of classes
+    # holds more subsets than the shared-memory stage and the list build
+    # places them directly; the joins see classes of several table fills.
     A, _, x = mi.generate(5, 46, 4646, planted=True, h=16)
     A = A.copy()
-    zero = list(range(9, 23))
-    A[:, zero] = 0
+    A[:2, 9:23] = 0
     d = (A.astype(np.int64) @ x.astype(np.int64)).astype(np.int32)
-    keep = [j for j in range(46) if j not in zero]
-    base = oracle.mitm(A[:, keep], d)
-    assert base
-    want = set()
-    for s in base:
-        v = sum(w << (64 * k) for k, w in enumerate(s))
-        full = sum(1 << keep[i] for i in range(len(keep)) if (v >> i) & 1)
-        for z in range(1 << len(zero)):
-            mask = full | sum(1 << zero[i] for i in range(len(zero)) if (z >> i) & 1)
-            want.add((mask,))  # n <= 64: one word
+    want = oracle.mitm(A, d)
+    assert mi.mask_of(x) in want
     got, st = solve(msp, A, d, {"direct": 1})
-    assert st["path"] == "direct" and st["class_bits"] == 10
-    assert sorted(got) == sorted(want)
+    assert st["path"] == "direct" and st["class_bits"] == 10 and st["direct_fallback"] == 0
+    assert got == want
 
 
 def test_streaming_pass_with_large_inner_quarters(msp):
