@@ -27,6 +27,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -233,8 +234,10 @@ def native(args, world, rank, local, pg):
     st0 = inst.stats()
     cand = st0["row1_candidates"]
 
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"), local)
+    # raw clock samples: $MSP_BENCH_OUT (default: the temporary directory)
+    out_dir = os.environ.get("MSP_BENCH_OUT") or tempfile.gettempdir()
+    os.makedirs(out_dir, exist_ok=True)
+    clk = ClockSampler(os.path.join(out_dir, f"clocks_rank{rank}.csv"), local)
     clk.start()
     kern = {}
     launches = 0
