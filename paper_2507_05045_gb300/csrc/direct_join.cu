@@ -45,6 +45,7 @@ size_t direct_smem_bytes(int TB, int noL, int noR) {
   return (size_t)4 * (tab_words(TB) + cnt_words(TB) + filt_words(TB) + claim_words(TB))
          + (size_t)kDW * 32 * 8         // per-warp element table
          + (size_t)kDW * 32 * 4         // per-warp start bitmaps
+         + (size_t)kDW * 32 * 4         // per-warp word bases
          + (size_t)kDW * kQueue * 4     // per-warp deferred keys
          + (size_t)kDW * 4              // per-warp left totals
          + 16;
@@ -75,13 +76,15 @@ __device__ __forceinline__ void emit_match(const DirectPass &p, bool e, uint32_t
 // inner keys of a batch are loaded together, so their latencies overlap.
 // Record k belongs to the last nonempty subset whose first record is <= k;
 // a bitmap marks the first records (1024 records per segment, one word per
-// lane) and a compacted per-warp table holds (start - first record, ka).
+// lane, with the count of first records before each word beside it) and a
+// compacted per-warp table holds (start - first record, ka).
 constexpr int kBatch = 4;
+static_assert(kBatch == 4, "a batch reads its bitmap words and bases as one uint4 each");
 
 template <typename F>
 __device__ __forceinline__ void group_records(uint32_t st, uint32_t len, uint32_t ka,
                                               const uint32_t *__restrict__ ikey, uint2 *et_w, uint32_t *bm_w,
-                                              uint32_t lo, uint32_t hi, F &&f) {
+                                              uint32_t *wb_w, uint32_t lo, uint32_t hi, F &&f) {
   const uint32_t ln = lane_id();
   const uint32_t ltmask = (1u << ln) - 1u;
   const uint32_t lemask = ltmask | (1u << ln);
@@ -103,8 +106,6 @@ __device__ __forceinline__ void group_records(uint32_t st, uint32_t len, uint32_
     if (len && pre >= S && pre - S < 1024u) atomicOr(bm_w + ((pre - S) >> 5), 1u << ((pre - S) & 31u));
     __syncwarp();
     const uint32_t myw = bm_w[ln];
-    __syncwarp();
-    bm_w[ln] = 0u;
     const uint32_t before = __popc(__ballot_sync(kFull, len != 0 && pre < S));
     const uint32_t pc = __popc(myw);
     uint32_t wi = pc;
@@ -114,16 +115,23 @@ __device__ __forceinline__ void group_records(uint32_t st, uint32_t len, uint32_
       if (ln >= static_cast<uint32_t>(o)) wi += y;
     }
     const uint32_t wbase = before + wi - pc;
+    wb_w[ln] = wbase;
+    __syncwarp();
     const uint32_t send = min(ke, S + 1024u);
     // inner key and outer key of each record of the batch at i0
     auto fetch = [&](uint32_t i0, uint32_t (&raw)[kBatch], uint32_t (&ko)[kBatch], uint32_t &okm) {
       okm = 0u;
+      // i0 - S is a multiple of 32 kBatch: the bitmap words and their bases
+      // of the batch's kBatch = 4 rows of 32 records in two broadcast loads
       const uint32_t w0 = (i0 - S) >> 5;
+      const uint4 wv = *reinterpret_cast<const uint4 *>(bm_w + w0);
+      const uint4 bv = *reinterpret_cast<const uint4 *>(wb_w + w0);
+      const uint32_t wa[kBatch] = {wv.x, wv.y, wv.z, wv.w};
+      const uint32_t ba[kBatch] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
       for (int b = 0; b < kBatch; ++b) {
-        const uint32_t w = (w0 + b) & 31u;
-        const uint32_t word = __shfl_sync(kFull, myw, w);
-        const uint32_t base = __shfl_sync(kFull, wbase, w);
+        const uint32_t word = wa[b];
+        const uint32_t base = ba[b];
         const uint32_t k = i0 + 32u * b + ln;
         const bool ok = k >= lo && k < send;
         const uint32_t c = base + __popc(word & lemask) - 1u;
@@ -142,6 +150,8 @@ __device__ __forceinline__ void group_records(uint32_t st, uint32_t len, uint32_
       for (int b = 0; b < kBatch; ++b) key[b] = kc[b] + rc[b];
       f(okc, key);
     }
+    __syncwarp();  // every lane has read this segment's words
+    bm_w[ln] = 0u;
   }
 }
 
@@ -158,7 +168,8 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
   uint32_t *const claim = F + filt_words(TB);
   uint2 *const et = reinterpret_cast<uint2 *>(claim + claim_words(TB));
   uint32_t *const wbm = reinterpret_cast<uint32_t *>(et + kDW * 32);
-  uint32_t *const wq = wbm + kDW * 32;      // [kDW][kQueue]
+  uint32_t *const wbb = wbm + kDW * 32;     // [kDW][32] record counts before each bitmap word
+  uint32_t *const wq = wbb + kDW * 32;      // [kDW][kQueue]
   uint32_t *const wtot = wq + kDW * kQueue;
   const int noL = p.no[0], noR = p.no[1];
   // per-class totals, double-buffered by class parity: class i accumulates
@@ -184,6 +195,7 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
   }
   uint2 *const et_w = et + wp * 32;
   uint32_t *const bm_w = wbm + wp * 32;
+  uint32_t *const wb_w = wbb + wp * 32;
   uint32_t *const q_w = wq + wp * kQueue;
   const uint32_t ltmask = (1u << ln) - 1u;
   uint32_t qn = 0;  // deferred keys of this warp (warp-uniform)
@@ -366,7 +378,7 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
             lo = a > woff ? a - woff : 0u;
             hi = b > woff ? b - woff : 0u;
           }
-          group_records(stL, lnL, kaL, ikeyL, et_w, bm_w, lo, hi,
+          group_records(stL, lnL, kaL, ikeyL, et_w, bm_w, wb_w, lo, hi,
                         [&](uint32_t okm, const uint32_t(&key)[kBatch]) {
 #pragma unroll
             for (int b = 0; b < kBatch; ++b) {
@@ -391,7 +403,7 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
         __syncthreads();
         // ---- right records: probe ----
         if (wp * 32 < static_cast<uint32_t>(noR)) {
-          group_records(stR, lnR, kaR, ikeyR, et_w, bm_w, 0u, 0xffffffffu,
+          group_records(stR, lnR, kaR, ikeyR, et_w, bm_w, wb_w, 0u, 0xffffffffu,
                         [&](uint32_t okm, const uint32_t(&key)[kBatch]) {
             uint32_t fw[kBatch];
 #pragma unroll
