@@ -202,9 +202,9 @@ def l2_note(st):
             "buffers of tens of GB")
 
 
-def traffic_per_launch(kernel, alg_bytes_per_launch):
-    """DRAM bytes per launch from the committed ncu capture, scaled by the
-    algorithmic bytes of a launch; None when the kernel source changed since."""
+def _capture(kernel):
+    """The committed ncu figures of a kernel, or None when its source changed
+    since they were taken."""
     import hashlib
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
@@ -212,9 +212,18 @@ def traffic_per_launch(kernel, alg_bytes_per_launch):
         src = open(os.path.join(ROOT, k["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest() != k["source_sha256"]:
             return None
-        return alg_bytes_per_launch * k["dram_bytes"] / k["algorithmic_bytes"]
+        return k
     except Exception:
         return None
+
+
+def traffic_per_launch(kernel, alg_bytes_per_launch):
+    """DRAM bytes per launch from the committed ncu capture, scaled by the
+    algorithmic bytes of a launch; None when the kernel source changed since."""
+    k = _capture(kernel)
+    if k is None:
+        return None
+    return alg_bytes_per_launch * k["dram_bytes"] / k["algorithmic_bytes"]
 
 
 def native(args, world, rank, local, pg):
@@ -305,6 +314,12 @@ def native(args, world, rank, local, pg):
                     "frac": None, "traffic": None, "peak_source": peak_src}
     if roof is not None and roof.get("bound") == "hbm":
         roof["traffic"] = traffic_per_launch(roof["kernel"], roof["bytes_per_launch"])
+        # the HBM fraction is low by design (no record reaches device memory):
+        # the on-chip limits of the same kernel source, from ncu
+        cap = _capture(roof["kernel"])
+        if cap is not None and "onchip" in cap:
+            roof["onchip"] = dict(cap["onchip"], source="ncu, profiles/" + cap["onchip"]["case"])
+            roof["onchip"].pop("case")
     for k, v in byte_kernels.items():
         v["achieved_gbs"] = v["bytes"] / (v["ms"] / 1000.0) / 1e9
         v["frac_of_measured_hbm"] = v["achieved_gbs"] / hbm_peak
