@@ -285,17 +285,23 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
   uint32_t kaL = 0, kaR = 0, clL = 0, clR = 0;
   uint32_t cur_inst = 0xffffffffu;
   uint32_t pfL0 = 0, pfL1 = 0, pfR0 = 0, pfR1 = 0;
-  auto load_bounds = [&](uint32_t r) {
-    pfL0 = pfL1 = pfR0 = pfR1 = 0u;
+  // carry: class r follows the previous class of the same work item, so a
+  // bucket starts where the previous one (r - 1) ended, unless the bucket
+  // index wrapped to 0
+  auto load_bounds = [&](uint32_t r, bool carry) {
     if (el < noL) {
       const uint32_t w = (r - clL) & cmask;
-      pfL0 = ioffL[w];
+      pfL0 = carry && w != 0u ? pfL1 : ioffL[w];
       pfL1 = ioffL[w + 1];
+    } else {
+      pfL0 = pfL1 = 0u;
     }
     if (el < noR) {
       const uint32_t w = (r - clR) & cmask;
-      pfR0 = ioffR[w];
+      pfR0 = carry && w != 0u ? pfR1 : ioffR[w];
       pfR1 = ioffR[w + 1];
+    } else {
+      pfR0 = pfR1 = 0u;
     }
   };
   uint32_t par = 0;                   // parity of the block's class count
@@ -325,9 +331,8 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
     const uint32_t rb = (item - ii * per_inst) * p.chunk, re = min(p.nclass, rb + p.chunk);
     for (uint32_t ri = rb; ri < re; ++ri, par ^= 1u) {
       const uint32_t r = (p.c0 + ri) & cmask;
-      // ---- bucket of this warp's outer subsets (lane = subset), loaded
-      //      during the previous class ----
-      load_bounds(r);
+      // ---- bucket of this warp's outer subsets (lane = subset) ----
+      load_bounds(r, ri > rb);
       const uint32_t stL = pfL0, lnL = pfL1 - pfL0, stR = pfR0, lnR = pfR1 - pfR0;
       unsigned long long sumL = lnL, sumR = lnR;
       bool big = lnL >= (1u << 24) || lnR >= (1u << 24);
