@@ -160,7 +160,7 @@ MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
 /*   MSP_OPT_DIRECT       the direct pass (default for every instance it
  *                        fits: halves of at most 40 columns): the columns of
  *                        each half are split into an outer quarter of at most
- *                        2^10 subsets and an inner quarter bucketed into
+ *                        2^9 subsets and an inner quarter bucketed into
  *                        residue classes of about 16 subsets, so a thread
  *                        block joins a whole class (about 2^13 records per
  *                        side) in shared memory and no record is written to
