@@ -1,7 +1,7 @@
 // Direct pass of libmsp, host side: the plan, the lists of an instance (or a
 // batch of instances), the launches of the class joins and the
-// verification, and the solves built from them (direct_kernels.cu holds the
-// kernels).
+// verification, and the solves built from them (direct_join.cu and
+// direct_kernels.cu hold the kernels).
 #include "direct_internal.cuh"
 #include "host_internal.h"
 #include "host_util.h"
