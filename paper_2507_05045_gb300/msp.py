@@ -45,6 +45,35 @@ class MspError(RuntimeError):
         self.code = code
 
 
+# device-memory budget of a solve or a server when the caller passes 0
+BUDGET_ENV = "MSP_MEMORY_BUDGET"
+_UNITS = {"": 1, "K": 1 << 10, "M": 1 << 20, "G": 1 << 30, "T": 1 << 40}
+
+
+def parse_bytes(text: str) -> int:
+    """A byte count: an integer with an optional K, M, G or T suffix
+    (powers of 1024, an optional trailing B), e.g. "150G", "1500MB", "4096"."""
+    t = str(text).strip().upper()
+    if t.endswith("B"):
+        t = t[:-1]
+    unit = t[-1:] if t[-1:] in _UNITS and t[-1:] != "" else ""
+    num = t[:-1] if unit else t
+    try:
+        value = float(num)
+    except ValueError:
+        raise MspError(-1, f"not a byte count: {text!r}") from None
+    if not (0 <= value < float(1 << 62)):  # also rejects nan and inf
+        raise MspError(-1, f"not a byte count: {text!r}")
+    return int(value * _UNITS[unit])
+
+
+def default_budget() -> int:
+    """$MSP_MEMORY_BUDGET in bytes, or 0 (the library's own default: 85 % of
+    the free device memory) when it is unset or empty."""
+    v = os.environ.get(BUDGET_ENV, "").strip()
+    return parse_bytes(v) if v else 0
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("quarter", ctypes.c_int * 4),
                 ("class_bits", ctypes.c_int), ("class_rows", ctypes.c_int), ("digit_bits", ctypes.c_int),
@@ -160,8 +189,11 @@ class Instance:
         and ``table_bits`` (direct pass; see MSP_OPT_* in msp.h), or
         ``"auto"`` for the autotuner's cached choice for this device and
         (m, n), if any.  ``first``: stop once a solution is found (direct
-        pass; MSP_OPT_FIRST)."""
+        pass; MSP_OPT_FIRST).  ``memory_budget``: bytes of device memory
+        the solve may use; 0 takes $MSP_MEMORY_BUDGET (e.g. "150G"), else
+        the library's default."""
         lib = load_library()
+        memory_budget = memory_budget or default_budget()
         A = np.asarray(A)
         if A.ndim != 2:
             raise MspError(-1, "A must be a 2-D matrix")
@@ -266,6 +298,7 @@ class Server:
 
     def __init__(self, hbm_budget: int = 0, max_inflight: int = 4):
         self._lib = load_library()
+        hbm_budget = hbm_budget or default_budget()
         h = ctypes.c_void_p()
         _check(self._lib.msp_server_create(ctypes.c_size_t(hbm_budget), max_inflight, ctypes.byref(h)))
         self._h = h
