@@ -173,22 +173,30 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append((float(parts[1]), float(parts[2]), parts[3], parts[5:9]))
-            except ValueError:
-                continue
-        if not rows:
-            return None
-        sm = sorted(r[0] for r in rows)
-        smax = max(r[1] for r in rows)
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
+        with open(self.path) as f:
+            return summarize_clocks(f)
+
+
+def summarize_clocks(lines):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in
+    nvidia-smi CSV rows of ClockSampler.FIELDS (no header, no units); None
+    without a parsable row."""
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            rows.append((float(parts[1]), float(parts[2]), parts[3], parts[5:9]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    sm = sorted(r[0] for r in rows)
+    smax = max(r[1] for r in rows)
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
 def l2_note(st):

@@ -1,0 +1,63 @@
+"""Host-side pieces of bench.py, on the CPU: the clock summary the JSON line
+carries, and the ncu traffic lookup keyed by the kernel source's sha256."""
+import hashlib
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+ROW = "0, {sm}, 2070, 600.0, 0x0000000000000000, {a}, {b}, {c}, {d}\n"
+
+
+def rows(*specs):
+    return [ROW.format(sm=sm, a=a, b=b, c=c, d=d) for sm, (a, b, c, d) in specs]
+
+
+QUIET = ("Not Active",) * 4
+
+
+def test_clock_summary_median_and_no_reason():
+    got = bench.summarize_clocks(rows((2070, QUIET), (1900, QUIET), (2070, QUIET)))
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+
+
+def test_clock_summary_reasons():
+    pc = ("Not Active", "Not Active", "Not Active", "Active")
+    th = ("Not Active", "Active", "Not Active", "Not Active")
+    got = bench.summarize_clocks(rows((2070, QUIET), (1800, pc), (1700, th)))
+    assert got["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert got["sm_mhz"] == 1800.0 and got["samples"] == 3
+
+
+def test_clock_summary_skips_bad_rows():
+    lines = ["garbage\n", "0, [N/A], 2070, 1, 0x0, Not Active, Not Active, Not Active, Not Active\n"]
+    assert bench.summarize_clocks(lines) is None
+    assert bench.summarize_clocks(lines + rows((2000, QUIET)))["samples"] == 1
+
+
+def test_traffic_lookup_follows_the_source_hash(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    entry = {"source": "k.cu", "source_sha256": hashlib.sha256(src.read_bytes()).hexdigest(),
+             "dram_bytes": 150, "algorithmic_bytes": 100,
+             "onchip": {"l1tex_pct_of_peak": 70.0, "case": "k.md"}}
+    (prof / "traffic.json").write_text(json.dumps({"kernels": {"k": entry}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_per_launch("k", 1000.0) == 1500.0
+    assert bench._capture("k")["onchip"]["l1tex_pct_of_peak"] == 70.0
+    assert bench.traffic_per_launch("other", 1000.0) is None
+    src.write_text("__global__ void k() { /* changed */ }\n")
+    assert bench.traffic_per_launch("k", 1000.0) is None
+    assert bench._capture("k") is None
+
+
+def test_committed_traffic_entries_name_existing_sources():
+    t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for name, k in t["kernels"].items():
+        assert os.path.exists(os.path.join(ROOT, k["source"])), name
+        assert os.path.exists(os.path.join(ROOT, "profiles", k["case"])), name
