@@ -268,6 +268,25 @@ MSP_API const char *msp_version(void);
  * the autotuner keys its cache by it. */
 MSP_API const char *msp_device_name(void);
 
+/* The plan msp_solve_all takes by default for an (m, n) instance, computed
+ * on the host (no device is needed; the memory check of a solve may still
+ * hand a direct-pass instance to the streaming pass). */
+typedef struct {
+  int path;              /* 1 = direct pass, 0 = streaming pass                  */
+  int class_bits;        /* residue classes: 2^class_bits                         */
+  int class_rows;        /* rows combined in the residue key                      */
+  int quarter[4];        /* q1..q4, L = Q1+Q3, R = Q2+Q4 (direct pass: outer L,
+                            outer R, inner L, inner R), as in msp_stats           */
+  int digit_bits;        /* streaming pass: radix digit bits (direct pass: 0)     */
+  int table_bits;        /* direct pass: 2^table_bits table slots (streaming: 0)  */
+  uint64_t records_left;  /* |L| = 2^(q1+q3)                                      */
+  uint64_t records_right; /* |R| = 2^(q2+q4)                                      */
+  uint64_t device_bytes;  /* estimated device memory of a solve, uncapped         */
+} msp_plan_info;
+/* MSP_OK, MSP_EINVAL (out is null) or MSP_ERANGE (m outside [1, 16] or n
+ * outside [1, 100]). */
+MSP_API int msp_plan(int m, int n, msp_plan_info *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,4 +5,4 @@ C ABI of ``include/msp.h``); this package only marshals arguments through
 ctypes.  See :mod:`paper_2507_05045_gb300.msp` for the Python API.
 """
 from .msp import (MspError, Instance, Server, solve_all, solve_batch, lib_path,  # noqa: F401
-                  load_library, solve_small_noalloc, EXPORTED_SYMBOLS)
+                  load_library, solve_small_noalloc, plan_info, EXPORTED_SYMBOLS)

@@ -798,6 +798,35 @@ const char *msp_last_error(void) { return g_err.c_str(); }
 
 const char *msp_version(void) { return "libmsp 0.1 (sm_103a)"; }
 
+int msp_plan(int m, int n, msp_plan_info *out) {
+  if (!out) return fail(MSP_EINVAL, "out must be non-null");
+  if (m < 1 || m > kMaxRows) return fail(MSP_ERANGE, "m must lie in [1, 16]");
+  if (n < 1 || n > kMaxN) return fail(MSP_ERANGE, "n must lie in [1, 100]");
+  std::memset(out, 0, sizeof(*out));
+  const DirectPlan dp = make_direct_plan(m, n, -1);
+  if (dp.ok) {
+    out->path = 1;
+    out->class_bits = dp.B;
+    out->class_rows = dp.t;
+    out->quarter[0] = dp.qo[0];
+    out->quarter[1] = dp.qo[1];
+    out->quarter[2] = dp.qi[0];
+    out->quarter[3] = dp.qi[1];
+    out->table_bits = dp.TB;
+  } else {
+    const Plan p = make_plan(m, n);
+    out->path = 0;
+    out->class_bits = p.B;
+    out->class_rows = p.t;
+    for (int k = 0; k < 4; ++k) out->quarter[k] = p.q[k];
+    out->digit_bits = p.D;
+  }
+  out->records_left = uint64_t(1) << (out->quarter[0] + out->quarter[2]);
+  out->records_right = uint64_t(1) << (out->quarter[1] + out->quarter[3]);
+  out->device_bytes = footprint_estimate(m, n, 0);
+  return MSP_OK;
+}
+
 const char *msp_device_name(void) {
   thread_local std::string name;
   name.clear();

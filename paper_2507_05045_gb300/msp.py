@@ -25,7 +25,7 @@ EXPORTED_SYMBOLS = (
     "msp_create", "msp_destroy", "msp_set_stream", "msp_set_memory_budget", "msp_solve_all",
     "msp_get_stats", "msp_free_solutions", "msp_set_profiling", "msp_set_option", "msp_solve_batch", "msp_server_create", "msp_submit",
     "msp_poll", "msp_cancel", "msp_server_destroy", "msp_last_error", "msp_version",
-    "msp_solve_small_noalloc", "msp_device_name", "msp_solve_batch_path",
+    "msp_solve_small_noalloc", "msp_device_name", "msp_solve_batch_path", "msp_plan",
 )
 
 # msp_set_option codes (include/msp.h)
@@ -106,6 +106,26 @@ class Stats(ctypes.Structure):
         return d
 
 
+class PlanInfo(ctypes.Structure):
+    """msp_plan_info (include/msp.h)."""
+    _fields_ = [("path", ctypes.c_int), ("class_bits", ctypes.c_int), ("class_rows", ctypes.c_int),
+                ("quarter", ctypes.c_int * 4), ("digit_bits", ctypes.c_int), ("table_bits", ctypes.c_int),
+                ("records_left", ctypes.c_uint64), ("records_right", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64)]
+
+
+def plan_info(m: int, n: int) -> dict:
+    """``msp_plan``: the plan a solve of an (m, n) instance takes by default
+    (host only, no device needed)."""
+    lib = load_library()
+    out = PlanInfo()
+    _check(lib.msp_plan(int(m), int(n), ctypes.byref(out)))
+    d = {k: getattr(out, k) for k, _ in PlanInfo._fields_}
+    d["quarter"] = list(out.quarter)
+    d["path"] = Stats.PATHS[out.path]
+    return d
+
+
 def lib_path() -> str:
     return _LIB_PATH
 
@@ -155,6 +175,8 @@ def load_library(path: str | None = None):
         lib.msp_last_error.restype = ctypes.c_char_p
         lib.msp_version.restype = ctypes.c_char_p
         lib.msp_device_name.restype = ctypes.c_char_p
+        lib.msp_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(PlanInfo)]
+        lib.msp_plan.restype = ctypes.c_int
         _lib = lib
         return lib
 

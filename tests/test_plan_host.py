@@ -1,0 +1,76 @@
+"""msp_plan: the default plan of an (m, n) instance, computed on the host.
+
+The expected plans follow the formulas of the two passes: the direct pass
+splits each half into an outer quarter of at most 9 columns and an inner
+quarter of B + 4 columns, B = max(0, log2 |half| - 13), whenever both halves
+have at most 40 columns; otherwise the streaming pass takes
+B = min(23, log2 |half| - 21) classes, inner quarters of B + 4 columns (at
+most 27) and D = min(12, log2 |half| - B - 12) digit bits.
+"""
+import ctypes
+
+import pytest
+
+import paper_2507_05045_gb300 as msp
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2507_05045_gb300 import build
+    build.build()
+
+
+def test_headline_shapes():
+    p = msp.plan_info(9, 80)
+    assert (p["path"], p["class_bits"], p["class_rows"], p["quarter"], p["table_bits"]) == \
+        ("direct", 27, 4, [9, 9, 31, 31], 14)
+    assert p["records_left"] == p["records_right"] == 1 << 40
+    # inner lists of 2 x 2^31 keys and masks, plus offsets and scratch
+    assert 2 * (1 << 31) * 8 < p["device_bytes"] < 60 << 30
+
+    p = msp.plan_info(10, 90)
+    assert (p["path"], p["class_bits"], p["class_rows"], p["quarter"], p["digit_bits"]) == \
+        ("streaming", 23, 4, [18, 18, 27, 27], 10)
+    assert p["records_left"] == p["records_right"] == 1 << 45
+
+    p = msp.plan_info(4, 30)
+    assert (p["path"], p["class_bits"], p["class_rows"], p["quarter"]) == ("direct", 2, 1, [9, 9, 6, 6])
+
+
+@pytest.mark.parametrize("m", [1, 3, 9, 16])
+def test_every_shape(m):
+    for n in range(1, 101):
+        p = msp.plan_info(m, n)
+        q = p["quarter"]
+        assert sum(q) == n
+        assert p["records_left"] == 1 << (q[0] + q[2]) and p["records_right"] == 1 << (q[1] + q[3])
+        assert 1 <= p["class_rows"] <= m
+        half = (n + 1) // 2
+        if 2 <= n and half <= 40:
+            B = max(0, half - 13)
+            assert p["path"] == "direct" and p["class_bits"] == B
+            for s, cols in ((0, half), (1, n - half)):
+                qi = min(cols, B + 4)
+                qo = cols - qi
+                if qo > 9:
+                    qo, qi = 9, cols - 9
+                assert (q[s], q[s + 2]) == (qo, qi)
+        else:
+            assert p["path"] == "streaming"
+            lg = max(q[0] + q[2], q[1] + q[3])
+            B = min(23, max(0, lg - 21))
+            assert p["class_bits"] == B
+            assert p["digit_bits"] == min(12, max(0, lg - B - 12))
+            assert max(q[2], q[3]) <= 27
+
+
+@pytest.mark.parametrize("m,n", [(0, 30), (17, 30), (4, 0), (4, 101)])
+def test_out_of_range(m, n):
+    with pytest.raises(msp.MspError) as e:
+        msp.plan_info(m, n)
+    assert e.value.code == -2
+
+
+def test_null_output_is_rejected():
+    lib = msp.load_library()
+    assert lib.msp_plan(4, 30, ctypes.POINTER(msp.msp.PlanInfo)()) == -1
