@@ -252,9 +252,11 @@ MSP_API void msp_server_destroy(msp_server *srv);
  *   the solutions exceed `cap` (then *count is an upper bound to retry with)
  *   or the static scratch (more than 8192 matched keys, 131072 candidates or
  *   131072 solutions).
- * The first call on a device resolves the array's address (with that device
- * current) and should come before any stream capture.  All calls share the
- * array, so calls that overlap on the GPU race: serialise them. */
+ * Every call looks up the array's address on the caller's current device, so
+ * a device reset between calls is harmless.  The call synchronises `stream`
+ * (it reads counts back between its phases), so it must not be made while
+ * that stream is capturing a CUDA graph.  All calls share the array, so calls
+ * that overlap on the GPU race: serialise them. */
 MSP_API int msp_solve_small_noalloc(const int32_t *A, const int32_t *d, int m, int n, uint64_t *masks,
                                     size_t cap, size_t *count, void *stream);
 

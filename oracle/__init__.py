@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
         os.path.getmtime(p) > os.path.getmtime(_LIB) for p in (_SRC, _HDR))
     if stale:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O3", "-std=gnu11", "-fopenmp", "-fPIC", "-shared",
                                "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
@@ -52,6 +52,9 @@ def _load():
             lib.msp_oracle_mitm.restype = ctypes.c_int64
             lib.msp_oracle_mitm.argtypes = [i32p, i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p,
                                             ctypes.c_int64]
+            lib.msp_oracle_fourlist.restype = ctypes.c_int64
+            lib.msp_oracle_fourlist.argtypes = [i32p, i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p,
+                                                ctypes.c_int64, ctypes.c_int64, u64p, ctypes.c_int64, u64p]
             lib.msp_oracle_subset_count.restype = ctypes.c_int
             lib.msp_oracle_subset_count.argtypes = [i32p, ctypes.c_int, ctypes.c_int64, u64p]
             lib.msp_oracle_residue_hist.restype = ctypes.c_int
@@ -71,14 +74,14 @@ def _masks(buf, count, words):
     return [tuple(int(w) for w in row) for row in arr]
 
 
-def _run(fn, A, d, m, n, *extra):
+def _run(fn, A, d, m, n, *extra, _after=()):
     words = (n + 63) // 64
     a, ap = _i32(np.asarray(A).reshape(m, n))
     dd, dp = _i32(np.asarray(d).reshape(m))
     cap = 1024
     while True:
         out = np.zeros(cap * words, dtype=np.uint64)
-        cnt = fn(ap, dp, m, n, *extra, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), cap)
+        cnt = fn(ap, dp, m, n, *extra, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), cap, *_after)
         if cnt < 0:
             raise RuntimeError(f"oracle failed with status {cnt}")
         if cnt <= cap:
@@ -106,6 +109,57 @@ def mitm(A, d, slices: int | None = None):
         slices = max(1, min(4096, (1 << max(0, half - 22))))
         slices = max(slices, os.cpu_count() or 1) if half >= 20 else slices
     return _run(_load().msp_oracle_mitm, A, d, m, n, int(slices))
+
+
+def default_slicing(m: int, n: int) -> tuple[int, ...]:
+    """Moduli of rows 1..4 for :func:`fourlist` giving slices of about 2^15
+    left subsets, so that one slice's hash table stays in a core's cache.
+    No modulus passes 2^7, well below the spread of a half's row sums in the
+    (m, 10 (m - 1)) family, so the slices are close to equal; with fewer rows
+    than needed the slices are simply larger."""
+    bits = max(0, n // 2 - 15)
+    t = max(1, min(m, 4))
+    per = [min(7, bits // t + (1 if k < bits % t else 0)) for k in range(t)]
+    return tuple(1 << b for b in per)
+
+
+def fourlist(A, d, mods=None, slice_range=None, return_records: bool = False):
+    """Sol(A, d) by the four-list meet in the middle over residue slices.
+
+    ``mods`` are the moduli P_1..P_t (t <= 4) of rows 1..t whose residue
+    tuple numbers the slices, s = r_1 + P_1 (r_2 + ...); ``slice_range``
+    = (s_begin, s_end) enumerates only those slices (default: all), which
+    gives exactly the solutions whose slice (:func:`slice_of`) lies in it.
+    With ``return_records`` the result is (solutions, left subsets, right
+    subsets enumerated).
+    """
+    A = np.asarray(A)
+    m, n = A.shape
+    if mods is None:
+        mods = default_slicing(m, n)
+    md, mp = _i32(mods)
+    S = int(np.prod(md)) if len(md) else 1
+    s0, s1 = (0, S) if slice_range is None else (int(slice_range[0]), int(slice_range[1]))
+    rec = np.zeros(2, dtype=np.uint64)
+    recp = rec.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    sols = _run(_load().msp_oracle_fourlist, A, d, m, n, len(md), mp, s0, s1, _after=(recp,))
+    if return_records:
+        return sols, int(rec[0]), int(rec[1])
+    return sols
+
+
+def slice_of(A, mask, mods) -> int:
+    """The slice of a solution mask in :func:`fourlist`: the residue tuple of
+    the row sums of its left half (columns 0 .. n/2 - 1) of rows 1..t."""
+    A = np.asarray(A, dtype=np.int64)
+    n = A.shape[1]
+    v = sum(int(w) << (64 * k) for k, w in enumerate(mask))
+    cols = [j for j in range(n // 2) if (v >> j) & 1]
+    s, stride = 0, 1
+    for k, P in enumerate(mods):
+        s += (int(A[k, cols].sum()) % int(P)) * stride
+        stride *= int(P)
+    return s
 
 
 def solve(A, d):

@@ -13,46 +13,39 @@
 // device array of kNoallocScratchBytes.  Every device that loads the library
 // holds that array until the process exits.
 //
-// Set-up: the first call on a device (with that device current) resolves
-// the array's device address with cudaGetSymbolAddress, once per device;
-// make that first call before any stream capture.  All calls share the one
-// array and it keeps the last call's contents, so the counters that must
-// start at zero are cleared on every call, and two calls that overlap on the
-// GPU (different streams or threads without ordering) race on it: serialise
-// them.
+// Set-up: every call resolves the array's device address on the caller's
+// current device with cudaGetSymbolAddress (a cheap lookup), so the address
+// stays right after a device reset reloads the module.  A call synchronises
+// its stream (it reads match, candidate and solution counts back to the host
+// between phases), so it must not be made while that stream is capturing a
+// CUDA graph.  All calls share the one array and it keeps the last call's
+// contents, so the counters that must start at zero are cleared on every
+// call, and two calls that overlap on the GPU (different streams or threads
+// without ordering) race on it: serialise them.
 #include "host_internal.h"
 
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 
 namespace {
 
 // 24 MiB: 2^20 eight-byte records per side (n <= 40) plus lists and tables.
 constexpr size_t kNoallocScratchBytes = size_t(24) << 20;
 constexpr int kNoallocMaxN = 40;
-constexpr int kNoallocMaxDevices = 64;
 constexpr uint64_t kNoallocMatchCap = 1u << 13;
 constexpr uint64_t kNoallocCandCap = 1u << 17;
 constexpr uint64_t kNoallocSolCap = 1u << 17;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-std::mutex g_setup_mu;
-void *g_scratch_addr[kNoallocMaxDevices] = {};
-
-// Device address of the scratch array on `dev` (the current device).
-int scratch_for(int dev, unsigned char **out) {
-  if (dev < 0 || dev >= kNoallocMaxDevices) return msp::fail(MSP_ERANGE, "device index out of range");
-  std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return msp::fail(MSP_ECUDA, std::string("cudaGetSymbolAddress of the scratch array: ") + cudaGetErrorString(e));
-    g_scratch_addr[dev] = p;
-  }
-  *out = static_cast<unsigned char *>(g_scratch_addr[dev]);
+// Device address of the scratch array on the current device, looked up on
+// every call.
+int scratch_address(unsigned char **out) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return msp::fail(MSP_ECUDA, std::string("cudaGetSymbolAddress of the scratch array: ") + cudaGetErrorString(e));
+  *out = static_cast<unsigned char *>(p);
   return MSP_OK;
 }
 
@@ -94,10 +87,8 @@ extern "C" int msp_solve_small_noalloc(const int32_t *A, const int32_t *d, int m
   if (n > kNoallocMaxN)
     return fail(MSP_ERANGE, "msp_solve_small_noalloc: n above 40 (its static scratch holds at most 2^20 "
                             "half-pair records per side); use msp_solve_all");
-  int dev = 0;
-  NA_CK(cudaGetDevice(&dev));
   unsigned char *scratch = nullptr;
-  rc = scratch_for(dev, &scratch);
+  rc = scratch_address(&scratch);
   if (rc != MSP_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 

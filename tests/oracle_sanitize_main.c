@@ -23,7 +23,7 @@ static uint64_t next_u64(void) { /* splitmix64: input generation only */
 #define MAXM 4
 #define CAP (1 << MAXN)
 
-static uint64_t out_b[CAP], out_m[CAP];
+static uint64_t out_b[CAP], out_m[CAP], out_f[CAP];
 
 int main(void) {
   int runs = 0;
@@ -54,6 +54,24 @@ int main(void) {
       const int64_t nm = msp_oracle_mitm(A, d, m, n, slices, out_m, CAP);
       if (nm != nb || memcmp(out_b, out_m, sizeof(uint64_t) * (size_t)nb) != 0) {
         printf("mitm != brute: seed %d slices %d (%lld vs %lld)\n", seed, slices, (long long)nm, (long long)nb);
+        return 1;
+      }
+      ++runs;
+    }
+    {
+      /* four-list meet in the middle over 0..3 residue rows of small moduli */
+      const int t = (int)(next_u64() % (uint64_t)((m < 3 ? m : 3) + 1));
+      int32_t fm[3];
+      int64_t S = 1;
+      for (int k = 0; k < t; ++k) {
+        fm[k] = 1 + (int32_t)(next_u64() % 5);
+        S *= fm[k];
+      }
+      uint64_t rec[2];
+      const int64_t nf = msp_oracle_fourlist(A, d, m, n, t, fm, 0, S, out_f, CAP, rec);
+      if (nf != nb || memcmp(out_b, out_f, sizeof(uint64_t) * (size_t)nb) != 0 ||
+          rec[0] != ((uint64_t)1 << (n / 2)) || rec[1] != ((uint64_t)1 << (n - n / 2))) {
+        printf("fourlist != brute: seed %d (%lld vs %lld)\n", seed, (long long)nf, (long long)nb);
         return 1;
       }
       ++runs;

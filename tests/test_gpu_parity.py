@@ -50,7 +50,7 @@ def load_golden(name):
     out = []
     for e in g["instances"]:
         A, d, x = mi.generate(e["m"], e["n"], e["seed"], planted=e["planted"], h=e["h"])
-        sols = [tuple(int(w, 16) for w in s) for s in e["solutions"]]
+        sols = [tuple(int(w, 16) for w in s) for s in e.get("solutions", [])]
         out.append((e, A, d, x, sols))
     return out
 
@@ -219,7 +219,7 @@ def test_many_passes_same_result(msp):
 
 
 @pytest.mark.parametrize("plan", PATHS)
-@pytest.mark.parametrize("name", ["sols_7_60.json", "sols_7_60_planted.json"])
+@pytest.mark.parametrize("name", ["sols_7_60.json", "sols_7_60_planted.json", "sols_7_60_more.json"])
 def test_config_7_60(msp, name, plan):
     for e, A, d, x, sols in load_golden(name):
         got, st = solve(msp, A, d, plan)
@@ -258,6 +258,32 @@ def _subcube_parity(msp_sols, A, d, fixed_cols, fixed_vals):
         if all(((v >> c) & 1) == b for c, b in zip(fixed_cols, fixed_vals)):
             got.append(v)
     assert sorted(got) == sorted(lifted)
+
+
+@pytest.mark.parametrize("plan", PATHS)
+def test_config_8_70_full_solution_sets(msp, plan):
+    # the plain and the planted (8,70) instance of seed 8: every solution,
+    # compared with the four-list oracle's full enumeration (2^36 records)
+    for e, A, d, x, sols in load_golden("sols_8_70.json"):
+        got, st = solve(msp, A, d, plan)
+        assert got == sols, (e["planted"], len(got), len(sols))
+        assert st["row1_candidates"] == oracle.row1_candidates(A, d)
+        if x is not None:
+            assert mi.mask_of(x) in got
+
+
+@pytest.mark.slow
+def test_config_9_80_bench_instance_full_solution_set(msp):
+    # the benchmark's plain (9,80) instance (seed 9080): every solution of the
+    # exhaustive solve, compared with the four-list oracle's full enumeration
+    # of all 2^41 half-subset records
+    for e, A, d, x, sols in load_golden("sols_9_80.json"):
+        with msp.Instance(A, d) as inst:
+            got = inst.solve_all()
+            st = inst.stats()
+        assert st["path"] == "direct"
+        assert got == sols
+        assert e["records"] == [1 << 40, 1 << 40]
 
 
 @pytest.mark.parametrize("plan", PATHS)
@@ -441,42 +467,45 @@ def test_inner_list_window_past_the_stage(msp):
 
 def test_streaming_pass_with_large_inner_quarters(msp):
     # the streaming pass with inner quarters of 27 columns (the shape the
-    # (10,90) configuration takes): the same solution set as the direct pass
-    A, d, x = mi.generate(8, 70, 81, planted=True, h=35)
-    plan = {"class_bits": 22, "digit_bits": 1, "inner_bits": 5, "direct": 0}
-    got, st = solve(msp, A, d, plan)
-    assert max(st["quarter"][2], st["quarter"][3]) == 27
-    want, st_d = solve(msp, A, d, {"direct": 1})
-    assert st_d["path"] == "direct"
-    assert got == want
-    assert mi.mask_of(x) in got
-    _check_solutions_exact(A, d, got)
+    # (10,90) configuration takes), on the (10,70) restriction of a planted
+    # (10,90) instance (20 seeded columns fixed to x*), against the oracle's
+    # full solution set of that restriction
+    for e, A, d, x, _ in load_golden("sols_10_70_subcube.json"):
+        A2, d2, free = mi.restrict(A, d, e["fixed_cols"], e["fixed_vals"])
+        want = [tuple(int(w, 16) for w in s) for s in e["solutions_restricted"]]
+        plan = {"class_bits": 22, "digit_bits": 1, "inner_bits": 5, "direct": 0}
+        got, st = solve(msp, A2, d2.astype(np.int32), plan)
+        assert max(st["quarter"][2], st["quarter"][3]) == 27
+        assert got == want
+        # x* restricted to the free columns is among them
+        xs = sum(1 << j for j, c in enumerate(free) if x[c])
+        assert (xs,) in got or (xs & ((1 << 64) - 1), xs >> 64) in got
+        assert solve(msp, A2, d2.astype(np.int32), {"direct": 1})[0] == want
 
 
 def test_first_solution_mode(msp):
-    # time-to-first: a nonempty subset of the full solution set, found before
-    # all classes are joined; an instance without solutions is searched to
-    # the end and returns none
-    A, d, x = mi.generate(8, 70, 8, planted=True, h=35)
-    full, st_full = solve(msp, A, d, {"direct": 1})
-    with msp.Instance(A, d, plan={"direct": 1}, first=True) as inst:
-        got = inst.solve_all()
-        st = inst.stats()
-    assert got and set(got) <= set(full)
-    _check_solutions_exact(A, d, got)
-    assert st["path"] == "direct"
-    assert 0 < st["classes_done"] <= st["classes_total"] == st_full["classes_total"]
-    assert st["records_done"] <= st_full["records_done"]
-    for seed in range(3):
-        A, d, _ = mi.generate(6, 50, 1000 + seed)
-        want = solve(msp, A, d, {"direct": 1})[0]
+    # time-to-first: a nonempty subset of the oracle's full solution set,
+    # found before all classes are joined; an instance without solutions is
+    # searched to the end and returns none
+    for e, A, d, x, sols in load_golden("sols_8_70.json"):
+        with msp.Instance(A, d, plan={"direct": 1}) as inst:
+            inst.solve_all()
+            st_full = inst.stats()
         with msp.Instance(A, d, plan={"direct": 1}, first=True) as inst:
             got = inst.solve_all()
             st = inst.stats()
-        if not want:
+        assert got and set(got) <= set(sols), e["planted"]
+        assert st["path"] == "direct"
+        assert 0 < st["classes_done"] <= st["classes_total"] == st_full["classes_total"]
+        assert st["records_done"] <= st_full["records_done"]
+    for e, A, d, x, sols in load_golden("sols_6_50_batch.json")[:3]:
+        with msp.Instance(A, d, plan={"direct": 1}, first=True) as inst:
+            got = inst.solve_all()
+            st = inst.stats()
+        if not sols:
             assert got == [] and st["classes_done"] == st["classes_total"]
         else:
-            assert got and set(got) <= set(want)
+            assert got and set(got) <= set(sols)
 
 
 def test_plan_options_are_validated(msp):

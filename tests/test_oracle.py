@@ -216,3 +216,116 @@ def test_generator_is_deterministic_and_in_range():
     # splitmix64 reference outputs for seed 0 (Steele, Lea, Flood 2014)
     g = mi.SplitMix64(0)
     assert [g.next() for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+# ---- the four-list oracle (slices of residue tuples of the first rows) ----
+
+def _random_mods(rng, m):
+    t = int(rng.integers(0, min(4, m) + 1))
+    return [int(x) for x in rng.integers(1, 8, size=t)]
+
+
+@pytest.mark.parametrize("seed", range(80))
+def test_fourlist_equals_numpy_enumeration(seed):
+    # any moduli (powers of two or not, t = 0..4 rows), small K with long runs
+    # of equal vectors, planted and plain right-hand sides
+    rng = np.random.default_rng(30_000 + seed)
+    m = int(rng.integers(1, 7))
+    n = int(rng.integers(1, 15))
+    K = int(rng.choice([2, 3, 5, 50, 100]))
+    A, d, _ = mi.generate(m, n, 3000 + seed, K=K, planted=bool(seed % 2), h=n // 2)
+    mods = _random_mods(rng, m)
+    sols, rl, rr = oracle.fourlist(A, d, mods=mods, return_records=True)
+    assert as_int(sols) == np_enumerate(A, d)
+    # every left and right subset is enumerated exactly once over all slices
+    assert (rl, rr) == (1 << (n // 2), 1 << (n - n // 2))
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_fourlist_equals_brute_n_up_to_24(seed):
+    rng = np.random.default_rng(31_000 + seed)
+    m = int(rng.integers(1, 11))
+    n = int(rng.integers(15, 25))
+    K = int(rng.choice([2, 5, 50, 100]))
+    A, d, _ = mi.generate(m, n, 3100 + seed, K=K, planted=bool(seed % 3), h=n // 2)
+    assert oracle.fourlist(A, d, mods=_random_mods(rng, m)) == oracle.brute(A, d)
+
+
+@pytest.mark.parametrize("m,n,seed", [(4, 30, 1), (4, 30, 2), (5, 36, 3), (5, 40, 4), (3, 34, 5)])
+def test_fourlist_equals_mitm(m, n, seed):
+    # halves past the inner split (outer parts of several columns), default
+    # slicing and a few others
+    A, d, _ = mi.generate(m, n, 3200 + seed, planted=True, h=n // 2)
+    want = oracle.mitm(A, d)
+    assert oracle.fourlist(A, d) == want
+    assert oracle.fourlist(A, d, mods=(3, 5)) == want
+    assert oracle.fourlist(A, d, mods=(1,)) == want
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_fourlist_slice_ranges_partition_the_set(seed):
+    # a range of slices gives exactly the solutions whose left-half residue
+    # tuple lies in it; disjoint ranges covering all slices give the full set
+    rng = np.random.default_rng(32_000 + seed)
+    m = int(rng.integers(2, 6))
+    n = int(rng.integers(12, 21))
+    A, d, _ = mi.generate(m, n, 3300 + seed, K=int(rng.choice([3, 5, 20])), planted=True, h=n // 2)
+    mods = [int(x) for x in rng.integers(2, 6, size=min(m, 3))]
+    S = int(np.prod(mods))
+    full = oracle.brute(A, d)
+    cuts = sorted(set([0, S] + [int(x) for x in rng.integers(0, S, size=3)]))
+    union, rec_l = [], 0
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        part, rl, _ = oracle.fourlist(A, d, mods=mods, slice_range=(a, b), return_records=True)
+        assert part == [x for x in full if a <= oracle.slice_of(A, x, mods) < b]
+        union += part
+        rec_l += rl
+    assert sorted(union) == full
+    assert rec_l == 1 << (n // 2)
+
+
+def test_fourlist_slice_of_by_hand():
+    # left half = columns 0, 1 of a 4-column instance; rows 1 and 2 mod (3, 2)
+    A = np.array([[2, 5, 7, 1], [1, 1, 4, 4]], dtype=np.int32)
+    # x = 0b0011: left sums (7, 2) -> residues (1, 0) -> slice 1
+    assert oracle.slice_of(A, (0b0011,), (3, 2)) == 1
+    # x = 0b0010: left sums (5, 1) -> (2, 1) -> 2 + 3 * 1 = 5
+    assert oracle.slice_of(A, (0b0010,), (3, 2)) == 5
+    # columns 2, 3 are the right half and never count
+    assert oracle.slice_of(A, (0b1100,), (3, 2)) == 0
+
+
+def test_fourlist_degenerate_inputs():
+    A = np.zeros((3, 9), dtype=np.int32)
+    assert as_int(oracle.fourlist(A, [0, 0, 0], mods=(2, 3))) == list(range(512))
+    assert oracle.fourlist(A, [0, 1, 0]) == []
+    A, d, _ = mi.generate(3, 16, 3)
+    d2 = d.copy()
+    d2[1] = A[1].sum() + 1
+    assert oracle.fourlist(A, d2, mods=(4, 4)) == []
+    assert oracle.fourlist(A, np.array([-1, 0, 0])) == []
+    # n = 1 and n = 2 (empty or one-column halves)
+    assert as_int(oracle.fourlist(np.array([[3]]), [3])) == [1]
+    assert as_int(oracle.fourlist(np.array([[3, 0]]), [3])) == [1, 3]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_fourlist_zero_column_and_row_permutation(seed):
+    A, d, _ = mi.generate(4, 22, 3400 + seed, K=4, planted=True, h=11)
+    sols = as_int(oracle.fourlist(A, d, mods=(4, 2)))
+    A2 = np.hstack([A, np.zeros((4, 1), dtype=np.int32)])
+    assert as_int(oracle.fourlist(A2, d, mods=(4, 2))) == sorted(sols + [s | (1 << 22) for s in sols])
+    perm = np.array([2, 0, 3, 1])
+    assert as_int(oracle.fourlist(A[perm], d[perm], mods=(3, 3))) == sols
+
+
+def test_fourlist_planted_at_size():
+    # the planted x* of a (6,50) instance is found with the default slicing,
+    # and the enumeration covers both halves exactly
+    A, d, x = mi.generate(6, 50, 21, planted=True, h=25)
+    sols, rl, rr = oracle.fourlist(A, d, return_records=True)
+    assert mi.mask_of(x) in sols
+    assert (rl, rr) == (1 << 25, 1 << 25)
+    for s in sols:
+        xv = _mask_to_x(s, 50)
+        assert np.array_equal(A.astype(np.int64) @ xv, d.astype(np.int64))
