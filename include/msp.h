@@ -191,8 +191,22 @@ enum {
   MSP_OPT_INNER_BITS = 6,
   MSP_OPT_DIRECT = 7,
   MSP_OPT_TABLE_BITS = 8,
-  MSP_OPT_FIRST = 9
+  MSP_OPT_FIRST = 9,
+  MSP_OPT_WAIT_LIMIT_US = 10,
+  MSP_OPT_WAIT_CHECK = 11
 };
+/*   MSP_OPT_WAIT_LIMIT_US  limit of each bounded wait of the streaming pass's
+ *                        join for a bulk copy, in microseconds, in [1, 6e7]
+ *                        (default 2e6, i.e. 2 s).  A wait that runs out sets
+ *                        an error flag, waits once more (bounded by the same
+ *                        limit) so that the copy lands before its block
+ *                        exits, and the solve returns MSP_ETIMEDOUT.
+ *   MSP_OPT_WAIT_CHECK   1 = check of that path: before its first copy, every
+ *                        block of the streaming join waits on a barrier phase
+ *                        that no copy completes, so the wait runs out and the
+ *                        solve returns MSP_ETIMEDOUT (with nothing in flight);
+ *                        the device and the library stay usable.  0 = off
+ *                        (default).  Neither changes any result. */
 MSP_API int msp_set_option(msp_instance *inst, int option, int64_t value);
 
 /* Time every kernel launch of later solves with CUDA events (on = 1). */

@@ -54,7 +54,8 @@ def _load():
                                             ctypes.c_int64]
             lib.msp_oracle_fourlist.restype = ctypes.c_int64
             lib.msp_oracle_fourlist.argtypes = [i32p, i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p,
-                                                ctypes.c_int64, ctypes.c_int64, u64p, ctypes.c_int64, u64p]
+                                                ctypes.c_int64, ctypes.c_int64, u64p, ctypes.c_int64, u64p,
+                                                ctypes.POINTER(ctypes.c_double)]
             lib.msp_oracle_subset_count.restype = ctypes.c_int
             lib.msp_oracle_subset_count.argtypes = [i32p, ctypes.c_int, ctypes.c_int64, u64p]
             lib.msp_oracle_residue_hist.restype = ctypes.c_int
@@ -123,7 +124,7 @@ def default_slicing(m: int, n: int) -> tuple[int, ...]:
     return tuple(1 << b for b in per)
 
 
-def fourlist(A, d, mods=None, slice_range=None, return_records: bool = False):
+def fourlist(A, d, mods=None, slice_range=None, return_records: bool = False, timing: dict | None = None):
     """Sol(A, d) by the four-list meet in the middle over residue slices.
 
     ``mods`` are the moduli P_1..P_t (t <= 4) of rows 1..t whose residue
@@ -131,7 +132,8 @@ def fourlist(A, d, mods=None, slice_range=None, return_records: bool = False):
     = (s_begin, s_end) enumerates only those slices (default: all), which
     gives exactly the solutions whose slice (:func:`slice_of`) lies in it.
     With ``return_records`` the result is (solutions, left subsets, right
-    subsets enumerated).
+    subsets enumerated).  A ``timing`` dict receives the seconds of the list
+    build ("build") and of the slice joins ("join").
     """
     A = np.asarray(A)
     m, n = A.shape
@@ -142,7 +144,11 @@ def fourlist(A, d, mods=None, slice_range=None, return_records: bool = False):
     s0, s1 = (0, S) if slice_range is None else (int(slice_range[0]), int(slice_range[1]))
     rec = np.zeros(2, dtype=np.uint64)
     recp = rec.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
-    sols = _run(_load().msp_oracle_fourlist, A, d, m, n, len(md), mp, s0, s1, _after=(recp,))
+    sec = np.zeros(2, dtype=np.float64)
+    secp = sec.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    sols = _run(_load().msp_oracle_fourlist, A, d, m, n, len(md), mp, s0, s1, _after=(recp, secp))
+    if timing is not None:
+        timing["build"], timing["join"] = float(sec[0]), float(sec[1])
     if return_records:
         return sols, int(rec[0]), int(rec[1])
     return sols

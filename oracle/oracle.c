@@ -40,6 +40,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <sys/mman.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -385,7 +386,8 @@ int msp_oracle_residue_hist(const int32_t *A, int m, int n, const int32_t *cols,
  * Only slices [s_begin, s_end) are enumerated (all of them give Sol(A, d);
  * any range gives the solutions whose slice lies in it).  records[0] and
  * records[1] receive the left and right subsets the run enumerated (2^nl and
- * 2^(n - nl) over all slices).
+ * 2^(n - nl) over all slices); seconds[0] and seconds[1] (when seconds is
+ * not NULL) the wall time of the list build and of the slice joins.
  */
 #define FL_INNER 30 /* inner columns per half at most */
 #define FL_OUTER 10 /* outer columns per half, when the inner part allows */
@@ -640,10 +642,18 @@ static inline int fl_equal(const int32_t *a, const int32_t *b, int m) {
   return 1;
 }
 
+static double fl_now(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
 int64_t msp_oracle_fourlist(const int32_t *A, const int32_t *d, int m, int n, int t, const int32_t *mods,
                             int64_t s_begin, int64_t s_end, uint64_t *out, int64_t cap,
-                            uint64_t *records) {
+                            uint64_t *records, double *seconds) {
   if (records) records[0] = records[1] = 0;
+  if (seconds) seconds[0] = seconds[1] = 0.0;
+  const double t_start = fl_now();
   if (m < 1 || m > 64 || n < 1 || n > 80 || t < 0 || t > FL_MAXT || t > m) return -1;
   fl_slicing sl;
   sl.t = t;
@@ -674,6 +684,7 @@ int64_t msp_oracle_fourlist(const int32_t *A, const int32_t *d, int m, int n, in
     return rc;
   }
   const fl_half *L = &H[0], *R = &H[1];
+  const double t_built = fl_now();
   int64_t count = 0;
   uint64_t recL = 0, recR = 0;
   int failed = 0;
@@ -818,6 +829,10 @@ int64_t msp_oracle_fourlist(const int32_t *A, const int32_t *d, int m, int n, in
       }
     }
     free(found.buf);
+  }
+  if (seconds) {
+    seconds[0] = t_built - t_start;
+    seconds[1] = fl_now() - t_built;
   }
   fl_half_free(&H[0]);
   fl_half_free(&H[1]);

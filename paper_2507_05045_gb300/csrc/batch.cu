@@ -372,6 +372,8 @@ int solve_batch_impl(const int32_t *const *A, const int32_t *const *d, int m, in
     fp.rec[1] = rec[1];
     fp.overflow = d_flags + 1;
     fp.error = d_flags;
+    fp.wait_ns = kDefaultWaitNs;
+    fp.wait_check = 0;
     fp.match_key = match_key;
     fp.match_cls = match_cls;
     fp.match_count = match_count;

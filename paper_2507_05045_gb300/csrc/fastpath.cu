@@ -622,15 +622,18 @@ __device__ __forceinline__ void issue_keys(const uint64_t *src, uint32_t n, uint
   if (bytes) bulk_load(dst, src, bytes, bar);
 }
 
-// Bounded wait on an mbarrier phase: thread 0 waits (2 s limit, then sets
-// the error flag and waits once more, bounded), the block learns the outcome
-// through shared memory, then every thread observes the completed phase.
-__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, unsigned int *err, int *s_ok) {
+// Bounded wait on an mbarrier phase: thread 0 waits (limit_ns, 2 s by
+// default; then it sets the error flag and waits once more, bounded by the
+// same limit, so that a copy still in flight lands before the block exits),
+// the block learns the outcome through shared memory, then every thread
+// observes the completed phase.
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, unsigned int *err, int *s_ok,
+                                           uint64_t limit_ns) {
   if (threadIdx.x == 0) {
     const uint64_t t0 = global_ns();
     bool ok = true;
     while (!mbar_try_wait(bar, parity)) {
-      if (global_ns() - t0 > 2000000000ull) {
+      if (global_ns() - t0 > limit_ns) {
         ok = false;
         break;
       }
@@ -638,7 +641,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, unsig
     if (!ok) {
       atomicOr(err, 1u);
       const uint64_t t1 = global_ns();
-      while (!mbar_try_wait(bar, parity) && global_ns() - t1 < 2000000000ull) {
+      while (!mbar_try_wait(bar, parity) && global_ns() - t1 < limit_ns) {
       }
     }
     *s_ok = ok ? 1 : 0;
@@ -730,10 +733,12 @@ __global__ void __launch_bounds__(kJT, 2) join_fast_kernel(FastPass p, int nseg)
   constexpr int nflag = kFastCap / 32 + 1;
   constexpr int nfp16 = kJBuckets * kJSlots / 8;  // fingerprint table in 16-byte words
   __shared__ __align__(8) uint64_t barL;
+  __shared__ __align__(8) uint64_t barCheck;
   __shared__ uint32_t s_novf;
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     mbar_init(&barL, 1);
+    mbar_init(&barCheck, 1);
     s_novf = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -741,6 +746,13 @@ __global__ void __launch_bounds__(kJT, 2) join_fast_kernel(FastPass p, int nseg)
   for (int i = threadIdx.x; i < nflag; i += kJT) flags[i] = 0;
   for (int i = threadIdx.x; i < nfp16; i += kJT) reinterpret_cast<uint4 *>(fps)[i] = make_uint4(0, 0, 0, 0);
   __syncthreads();
+  if (p.wait_check) {
+    // check of the bounded wait: a phase that expects 16 bytes no copy will
+    // deliver, so the wait runs out, sets the error flag and the block
+    // returns (no copy of this block is in flight yet)
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&barCheck, 16u);
+    if (!wait_phase(&barCheck, 0u, p.error, &s_ok, p.wait_ns)) return;
+  }
   const int G = gridDim.x;
   int s = blockIdx.x;
   if (s < nseg && threadIdx.x == 0) {
@@ -761,7 +773,7 @@ __global__ void __launch_bounds__(kJT, 2) join_fast_kernel(FastPass p, int nseg)
       const uint32_t pc = npair ? min(pi, npair - 1u) : 0u;
       rk[q] = npair ? __ldg(reinterpret_cast<const ulonglong2 *>(r.R) + pc) : make_ulonglong2(0, 0);
     }
-    if (!wait_phase(&barL, phL, p.error, &s_ok)) return;
+    if (!wait_phase(&barL, phL, p.error, &s_ok, p.wait_ns)) return;
     phL ^= 1u;
     // hash the left side
     for (uint32_t i = threadIdx.x; i < r.nL; i += kJT) {

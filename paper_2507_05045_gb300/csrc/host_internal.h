@@ -27,6 +27,8 @@ struct msp_instance {
   int direct = -1;      // direct pass: -1 auto, 0 never, 1 whenever the instance fits it
   int table_bits = -1;  // direct pass shared-table bits (-1 = default)
   bool first_only = false;  // direct pass: stop once a solution is found
+  uint64_t wait_ns = msp::kDefaultWaitNs;  // streaming join: limit of each bounded wait
+  int wait_check = 0;       // streaming join: each block first waits on a phase no copy completes
 };
 
 namespace msp {

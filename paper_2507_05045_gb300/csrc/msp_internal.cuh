@@ -116,6 +116,7 @@ struct FastInst {
   uint32_t tag;                   // added to the class id of emitted matches (instance * M)
 };
 
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;  // bounded waits of the streaming join: 2 s
 struct FastPass {
   const FastInst *inst;           // [ninst] in device memory
   int ninst;
@@ -126,6 +127,8 @@ struct FastPass {
   uint64_t *rec[2];
   unsigned int *overflow;         // [ninst]: the instance dropped a record (partition full)
   unsigned int *error;            // a bounded wait gave up
+  uint64_t wait_ns;               // limit of each bounded wait of the join
+  int wait_check;                 // 1: every join block first waits on a phase no copy completes
   uint64_t *match_key;
   uint32_t *match_cls;            // tag + class
   unsigned long long *match_count;

@@ -499,6 +499,8 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     fp.rec[0] = rec[0];
     fp.rec[1] = rec[1];
     fp.error = d_err;
+    fp.wait_ns = inst->wait_ns;
+    fp.wait_check = inst->wait_check;
     fp.match_key = match_key;
     fp.match_cls = match_cls;
     fp.match_count = match_count;
@@ -927,6 +929,14 @@ int msp_set_option(msp_instance *inst, int option, int64_t value) {
     case MSP_OPT_FIRST:
       if (value < 0 || value > 1) return fail(MSP_ERANGE, "first must be 0 or 1");
       inst->first_only = value != 0;
+      return MSP_OK;
+    case MSP_OPT_WAIT_LIMIT_US:
+      if (value < 1 || value > 60000000) return fail(MSP_ERANGE, "wait limit must lie in [1, 6e7] us");
+      inst->wait_ns = static_cast<uint64_t>(value) * 1000u;
+      return MSP_OK;
+    case MSP_OPT_WAIT_CHECK:
+      if (value < 0 || value > 1) return fail(MSP_ERANGE, "wait check must be 0 or 1");
+      inst->wait_check = static_cast<int>(value);
       return MSP_OK;
     case MSP_OPT_TABLE_BITS:
       if (value != -1 && (value < 12 || value > 15)) return fail(MSP_ERANGE, "table bits must be -1 or lie in [12, 15]");

@@ -32,6 +32,7 @@ EXPORTED_SYMBOLS = (
 OPT_EXACT_PATH, OPT_CLASS_PART, OPT_CLASS_PARTS = 1, 2, 3
 OPT_CLASS_BITS, OPT_DIGIT_BITS, OPT_INNER_BITS = 4, 5, 6
 OPT_DIRECT, OPT_TABLE_BITS, OPT_FIRST = 7, 8, 9
+OPT_WAIT_LIMIT_US, OPT_WAIT_CHECK = 10, 11
 PLAN_KEYS = {"class_bits": OPT_CLASS_BITS, "digit_bits": OPT_DIGIT_BITS, "inner_bits": OPT_INNER_BITS,
              "direct": OPT_DIRECT, "table_bits": OPT_TABLE_BITS}
 
@@ -205,7 +206,7 @@ class Instance:
 
     def __init__(self, A, d, stream: int | None = None, memory_budget: int = 0, profiling: bool = False,
                  exact_path: bool = False, class_part: tuple[int, int] | None = None, plan=None,
-                 first: bool = False):
+                 first: bool = False, wait_limit_us: int | None = None, wait_check: bool = False):
         """``plan``: None (built-in formulas), a dict with any of ``class_bits``,
         ``digit_bits``, ``inner_bits`` (streaming pass), ``direct`` (-1, 0, 1)
         and ``table_bits`` (direct pass; see MSP_OPT_* in msp.h), or
@@ -213,7 +214,9 @@ class Instance:
         (m, n), if any.  ``first``: stop once a solution is found (direct
         pass; MSP_OPT_FIRST).  ``memory_budget``: bytes of device memory
         the solve may use; 0 takes $MSP_MEMORY_BUDGET (e.g. "150G"), else
-        the library's default."""
+        the library's default.  ``wait_limit_us`` / ``wait_check``: the
+        streaming join's bounded-wait limit and its check mode
+        (MSP_OPT_WAIT_LIMIT_US, MSP_OPT_WAIT_CHECK)."""
         lib = load_library()
         memory_budget = memory_budget or default_budget()
         A = np.asarray(A)
@@ -238,6 +241,10 @@ class Instance:
             _check(lib.msp_set_option(h, 1, 1))
         if first:
             _check(lib.msp_set_option(h, OPT_FIRST, 1))
+        if wait_limit_us is not None:
+            _check(lib.msp_set_option(h, OPT_WAIT_LIMIT_US, int(wait_limit_us)))
+        if wait_check:
+            _check(lib.msp_set_option(h, OPT_WAIT_CHECK, 1))
         if class_part is not None:
             _check(lib.msp_set_option(h, OPT_CLASS_PARTS, int(class_part[1])))
             _check(lib.msp_set_option(h, OPT_CLASS_PART, int(class_part[0])))

@@ -91,21 +91,23 @@ def _fourlist_chunks(A, d, chunks, state_path, key):
     done = state.setdefault(key, {})
     for c in range(chunks):
         a, b = S * c // chunks, S * (c + 1) // chunks
-        if str(c) in done:
+        if f"{a}-{b}" in done:
             continue
         tc = time.time()
         sols, rl, rr = oracle.fourlist(A, d, mods=mods, slice_range=(a, b), return_records=True)
-        done[str(c)] = {"range": [a, b], "left": rl, "right": rr,
-                        "solutions": [[f"{w:016x}" for w in s] for s in sols]}
+        done[f"{a}-{b}"] = {"range": [a, b], "left": rl, "right": rr,
+                            "solutions": [[f"{w:016x}" for w in s] for s in sols]}
         if state_path:
             tmp = state_path + ".tmp"
             json.dump(state, open(tmp, "w"))
             os.replace(tmp, state_path)
         print(f"  {key} chunk {c + 1}/{chunks}: {len(sols)} solutions, {time.time() - tc:.1f}s", flush=True)
-    rl = sum(v["left"] for v in done.values())
-    rr = sum(v["right"] for v in done.values())
+    ranges = [S * c // chunks for c in range(chunks + 1)]
+    use = [done[f"{a}-{b}"] for a, b in zip(ranges[:-1], ranges[1:])]
+    rl = sum(v["left"] for v in use)
+    rr = sum(v["right"] for v in use)
     assert rl == 1 << (n // 2) and rr == 1 << (n - n // 2), (rl, rr)
-    sols = sorted({tuple(s) for v in done.values() for s in v["solutions"]},
+    sols = sorted({tuple(s) for v in use for s in v["solutions"]},
                   key=lambda t: tuple(int(w, 16) for w in reversed(t)))
     return [list(s) for s in sols]
 
@@ -161,7 +163,7 @@ def main():
         write("sols_7_60_more.json", entries_7_60_with_solutions(3, 70), "oracle.fourlist")
     if args.only == "9_80":
         state = args.state or os.path.join(HERE, "sols_9_80.state.json")
-        write("sols_9_80.json", [entry_fourlist(9, 80, SEED_9_80, False, None, 64, state)],
+        write("sols_9_80.json", [entry_fourlist(9, 80, SEED_9_80, False, None, 16, state)],
               "oracle.fourlist")
 
 

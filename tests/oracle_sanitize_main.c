@@ -68,7 +68,7 @@ int main(void) {
         S *= fm[k];
       }
       uint64_t rec[2];
-      const int64_t nf = msp_oracle_fourlist(A, d, m, n, t, fm, 0, S, out_f, CAP, rec);
+      const int64_t nf = msp_oracle_fourlist(A, d, m, n, t, fm, 0, S, out_f, CAP, rec, NULL);
       if (nf != nb || memcmp(out_b, out_f, sizeof(uint64_t) * (size_t)nb) != 0 ||
           rec[0] != ((uint64_t)1 << (n / 2)) || rec[1] != ((uint64_t)1 << (n - n / 2))) {
         printf("fourlist != brute: seed %d (%lld vs %lld)\n", seed, (long long)nf, (long long)nb);

@@ -33,9 +33,12 @@ def test_option_codes():
     assert msp.OPT_CLASS_PART == opts["MSP_OPT_CLASS_PART"]
     assert msp.OPT_CLASS_PARTS == opts["MSP_OPT_CLASS_PARTS"]
     assert msp.OPT_FIRST == opts["MSP_OPT_FIRST"]
+    assert msp.OPT_WAIT_LIMIT_US == opts["MSP_OPT_WAIT_LIMIT_US"]
+    assert msp.OPT_WAIT_CHECK == opts["MSP_OPT_WAIT_CHECK"]
     for key, code in msp.PLAN_KEYS.items():
         assert opts["MSP_OPT_" + key.upper()] == code
-    assert len(opts) == len(msp.PLAN_KEYS) + 4  # exact path, part, parts, first
+    # exact path, part, parts, first, wait limit, wait check
+    assert len(opts) == len(msp.PLAN_KEYS) + 6
 
 
 def test_kernel_kinds_in_index_order():
