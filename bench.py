@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--cols", "--n", dest="n", type=int, default=N_)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", choices=["9_80", "batch_6_50", "serving", "10_90_part", "profile_part",
-                                         "profile_small", "first_9_80"],
+                                         "profile_small", "first_9_80", "k_sweep"],
                     default="9_80",
                     help="9_80 (default): the headline exhaustive solve; batch_6_50: 64 (6,50) "
                          "instances in one batched call vs one at a time; serving: the mixed Poisson "
@@ -67,7 +67,8 @@ def parse():
                          "direct-pass solve of a (7,60) instance (lists of 8 MB), the case of the "
                          "full-section captures; first_9_80: time to the first solution (the "
                          "quantity of the paper's tables) of the plain bench instance and of a "
-                         "planted (9,80) instance")
+                         "planted (9,80) instance; k_sweep: plain (8,70) and (9,80) instances with "
+                         "a_ij in [0, K) for K = 50, 100, 200 (the paper's (m, n, K) classes)")
     ap.add_argument("--path", type=int, default=1, choices=[0, 1],
                     help="profile_part: 1 = direct pass, 0 = streaming pass")
     ap.add_argument("--requests", type=int, default=512)
@@ -659,6 +660,39 @@ def bench_first(args):
            "paper": "236.07 s average over four QOBLIB (9,80,100) instances, hybrid CPU+H200 (Table 1)"})
 
 
+def bench_k_sweep(args):
+    """The coefficient range K of the paper's (m, n, K) classes (Table 1):
+    plain (8,70) and (9,80) instances with a_ij in [0, K) for K in
+    {50, 100, 200}, each solved exhaustively on the direct pass; reports the
+    time to all solutions, C1, the matched keys checked exactly and the
+    solutions."""
+    import paper_2507_05045_gb300 as msp
+    from paper_2507_05045_gb300 import build
+    build.build()
+    rows = []
+    for (m, n) in ((8, 70), (9, 80)):
+        for K in (50, 100, 200):
+            A, d, _ = mi.generate(m, n, SEED if (m, n) == (M_, N_) else 8, K=K)
+            with msp.Instance(A, d, profiling=True) as inst:
+                for _ in range(args.warmup):
+                    inst.solve_all()
+                ts = []
+                for _ in range(args.steps):
+                    t0 = time.perf_counter()
+                    sols = inst.solve_all()
+                    ts.append(time.perf_counter() - t0)
+                st = inst.stats()
+            rows.append({"class": f"({m},{n},{K})", "seed": SEED if (m, n) == (M_, N_) else 8,
+                         "time_to_all_s": float(np.median(ts)), "row1_candidates": st["row1_candidates"],
+                         "key_matches": st["key_matches"], "pairs_verified": st["pairs_verified"],
+                         "solutions": len(sols), "path": st["path"], "class_bits": st["class_bits"]})
+    _emit({"metric": "time to all solutions over the coefficient range K (Table 1 classes)",
+           "value": rows[-2]["time_to_all_s"], "unit": "s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": False, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": "plain (8,70) seed 8 and (9,80) seed 9080, a_ij in [0, K), K = 50, 100, 200"},
+           "classes": rows})
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_init(args)
@@ -683,6 +717,9 @@ def main():
         elif args.config == "first_9_80":
             if rank == 0:
                 bench_first(args)
+        elif args.config == "k_sweep":
+            if rank == 0:
+                bench_k_sweep(args)
         else:
             native(args, world, rank, local, pg)
     finally:

@@ -118,7 +118,9 @@ enum {
 };
 
 /* Validate and copy (A row-major m x n, d length m); upload to the device.
- * On success *out owns the instance (free with msp_destroy). */
+ * A and d are the matrix and right-hand side of the system A x = d over
+ * x in {0,1}^n (Section 1, eq. 1; a_ij and d_i in N0).  On success *out owns
+ * the instance (free with msp_destroy). */
 MSP_API int msp_create(const int32_t *A, const int32_t *d, int m, int n, msp_instance **out);
 
 /* Release an instance and its device memory (NULL is ignored). */
@@ -212,8 +214,16 @@ MSP_API int msp_set_option(msp_instance *inst, int option, int64_t value);
 /* Time every kernel launch of later solves with CUDA events (on = 1). */
 MSP_API int msp_set_profiling(msp_instance *inst, int on);
 
-/* Exhaustive solve: every x with A x = d.  Blocking.  *masks is allocated by
- * the library (free with msp_free_solutions; NULL when *count is 0). */
+/* Exhaustive solve: every x with A x = d, the set of Section 1, eq. 1 (the
+ * paper's Algorithm 2 stops at the first; this call returns all of them
+ * unless MSP_OPT_FIRST is set).  The four quarter lists of Algorithm 1 are
+ * built on the device, the half-pairs joined by residue class (eq. 2's
+ * surrogate idea as the class key) and every key match checked on all m rows
+ * (Algorithm 3's validation).  Blocking.  *masks is allocated by the library
+ * (free with msp_free_solutions; NULL when *count is 0); *words_per_mask is
+ * ceil(n/64).  Errors: MSP_EINVAL (null argument), MSP_ENOMEM (the memory
+ * budget holds no pass), MSP_ECUDA, MSP_ETIMEDOUT, MSP_EOVERFLOW,
+ * MSP_ECANCELED (serving loop only). */
 MSP_API int msp_solve_all(msp_instance *inst, uint64_t **masks, size_t *count, int *words_per_mask);
 
 /* Counters of the last solve of this instance. */
@@ -223,7 +233,8 @@ MSP_API int msp_get_stats(const msp_instance *inst, msp_stats *out);
 MSP_API void msp_free_solutions(uint64_t *masks);
 
 /* Solve `count` independent instances of the same (m, n): A[k] and d[k]
- * point to instance k.  Solutions of instance k are masks[offsets[k] ..
+ * point to instance k, and its result is eq. 1's set for (A[k], d[k]) (the
+ * paper solves one instance at a time; batching has no counterpart there).  Solutions of instance k are masks[offsets[k] ..
  * offsets[k+1]) in units of masks (each ceil(n/64) words); offsets has
  * count+1 entries; *masks is library-allocated (msp_free_solutions). */
 MSP_API int msp_solve_batch(const int32_t *const *A, const int32_t *const *d, int m, int n, int count,
@@ -238,9 +249,17 @@ MSP_API int msp_solve_batch(const int32_t *const *A, const int32_t *const *d, in
 MSP_API int msp_solve_batch_path(const int32_t *const *A, const int32_t *const *d, int m, int n, int count,
                                  int path, uint64_t **masks, size_t *offsets);
 
-/* Serving: a request queue whose instances share the device.  Requests are
- * admitted while their next residue pass fits the memory budget, and the
- * passes of admitted requests are interleaved on several streams. */
+/* Serving: a request queue whose instances share the device (no counterpart
+ * in the paper; each request's result is eq. 1's set for its instance, the
+ * same as msp_solve_all's).  Requests are admitted while their device
+ * footprint fits the memory budget, and the passes of admitted requests are
+ * interleaved on several streams.
+ *   msp_server_create: hbm_budget_bytes 0 = 80% of the free device memory;
+ *     max_inflight in [1, 64] workers.  MSP_ECUDA without a device.
+ *   msp_submit: A, d as for msp_create, copied; *req_id identifies the
+ *     request.  MSP_ENOMEM when its footprint exceeds the whole budget.
+ *   msp_cancel: a queued request is dropped, a running one stops at its next
+ *     launch boundary; its msp_poll then returns MSP_ECANCELED. */
 MSP_API int msp_server_create(size_t hbm_budget_bytes, int max_inflight, msp_server **out);
 MSP_API int msp_submit(msp_server *srv, const int32_t *A, const int32_t *d, int m, int n, uint64_t *req_id);
 /* MSP_PENDING while running; MSP_OK with the solutions once done (masks as in

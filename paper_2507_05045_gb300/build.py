@@ -3,6 +3,9 @@
 Compiles every ``csrc/*.cu`` translation unit with nvcc in parallel and links
 them into ``paper_2507_05045_gb300/libmsp.so`` (in-tree; the object files go
 to ``paper_2507_05045_gb300/_build/``).  Rebuilds only what is stale.
+``build(checked=True)`` builds ``libmsp_checked.so`` instead, with
+``-DMSP_CHECKED``: the kernels then test their data-dependent indices
+before every access, and a failed check fails the solve (csrc/checked.cuh).
 """
 from __future__ import annotations
 
@@ -17,6 +20,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmsp.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libmsp_checked.so")
 HEADERS = [os.path.join(ROOT, "include", "msp.h")] + glob.glob(os.path.join(CSRC, "*.h")) + \
     glob.glob(os.path.join(CSRC, "*.cuh"))
 
@@ -39,17 +44,20 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    build_dir = BUILD_CHECKED if checked else BUILD
+    lib_path = LIB_CHECKED if checked else LIB
+    flags = FLAGS + (["-DMSP_CHECKED"] if checked else [])
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     cc = nvcc()
     jobs = []
     objs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(build_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + HEADERS):
-            jobs.append([cc, *ARCH, *FLAGS, "-c", s, "-o", o])
+            jobs.append([cc, *ARCH, *flags, "-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             res = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
@@ -59,15 +67,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 print(r.stdout, r.stderr)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             print(r.stdout, r.stderr)
             raise RuntimeError("linking libmsp.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -234,6 +234,7 @@ int solve_batch_impl(const int32_t *const *A, const int32_t *const *d, int m, in
       g.ocls = o.cls;
       g.osize = o.size;
       g.ikey = in.key;
+      g.isize = in.size;
       g.ioff = in.off;
       const int64_t per_bucket = std::max<int64_t>(1, in.size / M);
       g.slice_outer = std::max<int64_t>(1, (int64_t(1) << 19) / per_bucket);

@@ -63,8 +63,7 @@ namespace {
 
 // Host and device lists of one instance of a direct pass.
 struct DirectLists {
-  std::vector<uint32_t> okey[2], ocls[2], omask[2];
-  std::vector<uint64_t> ovec[2];
+  int no[2] = {0, 0};  // outer subsets per side
   uint64_t dvec[4] = {0, 0, 0, 0};
   uint32_t *ikey[2] = {nullptr, nullptr}, *imask[2] = {nullptr, nullptr}, *ioff[2] = {nullptr, nullptr};
   uint64_t *icol[2] = {nullptr, nullptr};
@@ -85,16 +84,12 @@ struct Copier {
   }
 };
 
-// S0 + S1 + S2 of one instance: column keys and classes, the outer lists
-// (host, at most 2^9 subsets each), the inner lists bucketed by class
-// (device: count, offsets, scatter).  `cnt` and `scantmp` are scratch of
-// 2^B + 1 and (2^B + 1) / 4096 + 1 entries, shared by successive calls.
-// S0 + S1 on the host for one instance: the column keys and classes, the
-// outer lists (at most 2^9 subsets each), the packed right-hand side, and
-// the column tables g[side] and packed column vectors icol[side] of the
-// inner quarters.
+// S0 on the host for one instance: the column keys and classes, the packed
+// right-hand side, the column tables of the outer quarters o[side] (their
+// lists are built on the device) and of the inner quarters g[side], and the
+// packed column vectors icol[side] of the inner quarters.
 void prep_direct_host(const int32_t *A, const int32_t *d, int m, int n, const DirectPlan &dp, const Plan &kp,
-                      DirectLists &L, InnerGen g[2], std::vector<uint64_t> icol[2]) {
+                      DirectLists &L, OuterSeg o[2], InnerGen g[2], std::vector<uint64_t> icol[2]) {
   const uint32_t M = 1u << dp.B, cmask = M - 1u;
   std::vector<uint32_t> ck(n), cc(n);
   std::vector<uint64_t> pc((size_t)n * 4, 0);
@@ -118,23 +113,18 @@ void prep_direct_host(const int32_t *A, const int32_t *d, int m, int n, const Di
   }
   for (int sd = 0; sd < 2; ++sd) {
     const int q = dp.qo[sd], c0 = dp.col_o[sd];
-    const uint32_t no = 1u << q;
-    L.okey[sd].resize(no);
-    L.ocls[sd].resize(no);
-    L.omask[sd].resize(no);
-    L.ovec[sd].assign((size_t)no * 4, 0);
-    for (uint32_t u = 0; u < no; ++u) {
-      uint32_t k = 0, c = 0;
-      for (int j = 0; j < q; ++j)
-        if (u >> j & 1u) {
-          k += ck[c0 + j];
-          c += cc[c0 + j];
-          for (int w = 0; w < 4; ++w) L.ovec[sd][(size_t)u * 4 + w] += pc[(size_t)(c0 + j) * 4 + w];
-        }
-      L.okey[sd][u] = sd ? kd - k : k;
-      L.ocls[sd][u] = (sd ? cd - c : c) & cmask;
-      L.omask[sd][u] = u;
+    L.no[sd] = 1 << q;
+    o[sd] = OuterSeg{};
+    for (int j = 0; j < q; ++j) {
+      o[sd].ck[j] = ck[c0 + j];
+      o[sd].cc[j] = cc[c0 + j];
+      for (int w = 0; w < 4; ++w) o[sd].pc[j][w] = pc[(size_t)(c0 + j) * 4 + w];
     }
+    o[sd].q = q;
+    o[sd].neg = sd;
+    o[sd].kd = kd;
+    o[sd].cd = cd;
+    o[sd].cmask = cmask;
   }
   for (int sd = 0; sd < 2; ++sd) {
     const int q = dp.qi[sd], c0 = dp.col_i[sd];
@@ -162,8 +152,9 @@ int build_direct_lists(const int32_t *A, const int32_t *d, int m, int n, const D
   cudaStream_t s = cp.s;
   const uint32_t M = 1u << dp.B;
   InnerGen gs[2];
+  OuterSeg os[2];
   std::vector<uint64_t> icol[2];
-  prep_direct_host(A, d, m, n, dp, kp, L, gs, icol);
+  prep_direct_host(A, d, m, n, dp, kp, L, os, gs, icol);
   for (int sd = 0; sd < 2; ++sd) {
     const int q = dp.qi[sd];
     const uint64_t ni = uint64_t(1) << q;
@@ -216,17 +207,22 @@ int build_direct_lists(const int32_t *A, const int32_t *d, int m, int n, const D
     da.free1(lcur, sizeof(uint32_t) * ((size_t)w.nc + 1));
     da.free1(low, sizeof(uint4) * nl);
   }
+  // S1 of the outer quarters on the device
   for (int sd = 0; sd < 2; ++sd) {
-    const size_t no = L.okey[sd].size();
+    const size_t no = static_cast<size_t>(L.no[sd]);
     CK(da.get(&L.d_okey[sd], no));
     CK(da.get(&L.d_ocls[sd], no));
     CK(da.get(&L.d_omask[sd], no));
     CK(da.get(&L.d_ovec[sd], no * 4));
-    CK(cp.h2d(L.d_okey[sd], L.okey[sd].data(), 4 * no));
-    CK(cp.h2d(L.d_ocls[sd], L.ocls[sd].data(), 4 * no));
-    CK(cp.h2d(L.d_omask[sd], L.omask[sd].data(), 4 * no));
-    CK(cp.h2d(L.d_ovec[sd], L.ovec[sd].data(), 8 * 4 * no));
+    os[sd].okey = L.d_okey[sd];
+    os[sd].ocls = L.d_ocls[sd];
+    os[sd].omask = L.d_omask[sd];
+    os[sd].ovec = L.d_ovec[sd];
   }
+  OuterSeg *d_os;
+  CK(da.get(&d_os, 2));
+  CK(cp.h2d(d_os, os, sizeof(OuterSeg) * 2));
+  LAUNCH(MSP_K_GRAY, 1, 0, launch_direct_outer(d_os, 2, s));
   return MSP_OK;
 }
 
@@ -242,20 +238,17 @@ int build_direct_lists_batch(const int32_t *const *A, const int32_t *const *d, c
   const uint32_t M = 1u << dp.B;
   lists.assign(K, DirectLists{});
   std::vector<InnerSeg> segs(2 * K);  // segment side * K + k
+  std::vector<OuterSeg> osegs(2 * K);
   std::vector<uint64_t> icol_h[2];
-  std::vector<uint32_t> ok_h[2], oc_h[2], om_h[2];
-  std::vector<uint64_t> ov_h[2];
   for (size_t k = 0; k < K; ++k) {
     InnerGen g[2];
+    OuterSeg o[2];
     std::vector<uint64_t> icol[2];
-    prep_direct_host(A[idx[k]], d[idx[k]], m, n, dp, kp, lists[k], g, icol);
+    prep_direct_host(A[idx[k]], d[idx[k]], m, n, dp, kp, lists[k], o, g, icol);
     for (int sd = 0; sd < 2; ++sd) {
       segs[sd * K + k].g = g[sd];
+      osegs[sd * K + k] = o[sd];
       icol_h[sd].insert(icol_h[sd].end(), icol[sd].begin(), icol[sd].end());
-      ok_h[sd].insert(ok_h[sd].end(), lists[k].okey[sd].begin(), lists[k].okey[sd].end());
-      oc_h[sd].insert(oc_h[sd].end(), lists[k].ocls[sd].begin(), lists[k].ocls[sd].end());
-      om_h[sd].insert(om_h[sd].end(), lists[k].omask[sd].begin(), lists[k].omask[sd].end());
-      ov_h[sd].insert(ov_h[sd].end(), lists[k].ovec[sd].begin(), lists[k].ovec[sd].end());
     }
   }
   for (int sd = 0; sd < 2; ++sd) {
@@ -274,10 +267,6 @@ int build_direct_lists_batch(const int32_t *const *A, const int32_t *const *d, c
     CK(da.get(&omask, no * K));
     CK(da.get(&ovec, 4 * no * K));
     CK(cp.h2d(icol, icol_h[sd].data(), 8 * icol_h[sd].size()));
-    CK(cp.h2d(okey, ok_h[sd].data(), 4 * no * K));
-    CK(cp.h2d(ocls, oc_h[sd].data(), 4 * no * K));
-    CK(cp.h2d(omask, om_h[sd].data(), 4 * no * K));
-    CK(cp.h2d(ovec, ov_h[sd].data(), 32 * no * K));
     CK(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * M * K, s));
     for (size_t k = 0; k < K; ++k) {
       DirectLists &L = lists[k];
@@ -289,6 +278,11 @@ int build_direct_lists_batch(const int32_t *const *A, const int32_t *const *d, c
       L.d_ocls[sd] = ocls + no * k;
       L.d_omask[sd] = omask + no * k;
       L.d_ovec[sd] = ovec + 4 * no * k;
+      OuterSeg &O = osegs[sd * K + k];
+      O.okey = L.d_okey[sd];
+      O.ocls = L.d_ocls[sd];
+      O.omask = L.d_omask[sd];
+      O.ovec = L.d_ovec[sd];
       InnerSeg &S = segs[sd * K + k];
       S.cnt = cnt + (size_t)M * k;
       S.ioff = L.ioff[sd];
@@ -296,6 +290,11 @@ int build_direct_lists_batch(const int32_t *const *A, const int32_t *const *d, c
       S.imask = L.imask[sd];
     }
   }
+  // S1 of every outer quarter of the batch on the device: one launch
+  OuterSeg *d_osegs;
+  CK(da.get(&d_osegs, 2 * K));
+  CK(cp.h2d(d_osegs, osegs.data(), sizeof(OuterSeg) * 2 * K));
+  LAUNCH(MSP_K_GRAY, 1, 0, launch_direct_outer(d_osegs, static_cast<int>(2 * K), s));
   InnerSeg *d_segs;
   CK(da.get(&d_segs, 2 * K));
   CK(cp.h2d(d_segs, segs.data(), sizeof(InnerSeg) * 2 * K));
@@ -345,7 +344,8 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
       ds.ocls = L.d_ocls[sd];
       ds.ikey = L.ikey[sd];
       ds.ioff = L.ioff[sd];
-      ds.no = static_cast<int>(L.okey[sd].size());
+      ds.no = L.no[sd];
+      ds.ni = static_cast<uint32_t>(std::min<uint64_t>(uint64_t(1) << dp.qi[sd], 0xffffffffull));
       DirectVerifyInst &vi = vtab[k];
       vi.side[sd] = ds;
       vi.imask[sd] = L.imask[sd];
@@ -431,6 +431,7 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
       v.sol_cap = cap;
       CK(cudaMemsetAsync(cnts, 0, (1 + kVerifyPairSlots) * sizeof(unsigned long long), s));
       CK(cudaMemsetAsync(ovf, 0, sizeof(unsigned int), s));
+      NvtxRange nv("msp direct: verification");
       LAUNCH(MSP_K_VERIFY, 1, 0, launch_direct_verify(v, static_cast<unsigned>(m1 - m0), s));
       unsigned long long hcs[1 + kVerifyPairSlots];
       unsigned int ovf_h = 0;
@@ -467,8 +468,16 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
   int passes = 0;
   uint64_t verified_to = 0;  // first-solution mode: matches verified so far
   uint32_t classes_run = 0;
+  // A cancelable solve (serving loop) keeps at most kInFlight join launches
+  // queued, so that a cancellation seen before a launch stops the solve
+  // within a few launches; other solves queue every launch at once.
+  constexpr uint32_t kInFlight = 2;
+  EventRing ring(cancel ? kInFlight : 0);
   for (uint32_t li = 0; li < nlaunch; ++li) {
-    if (cancel && *cancel) return fail(MSP_ECANCELED, "request canceled");
+    if (cancel) {
+      if (li >= kInFlight) CK(ring.wait(li % kInFlight));
+      if (*cancel) return fail(MSP_ECANCELED, "request canceled");
+    }
     p.c0 = c_begin + li * per_launch;
     p.nclass = std::min(per_launch, c_end - p.c0);
     p.work = work + li;
@@ -478,6 +487,7 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
     const double rec_est = (double)K * p.nclass * rec_per_class;
     LAUNCH(MSP_K_DIRECT, 1, static_cast<uint64_t>(4.0 * rec_est + per_class_in * p.nclass * K),
            launch_direct_join(dp.TB, p, s));
+    if (cancel) CK(ring.record(li % kInFlight, s));
     ++passes;
     classes_run += p.nclass;
     if (first) {
@@ -544,6 +554,7 @@ int solve_direct(msp_instance *inst, const DirectPlan &dp, const Plan &kp, size_
   Copier cp{&st, s};
   std::vector<DirectLists> lists(1);
   {
+    NvtxRange nv("msp direct: quarter lists");
     uint32_t *cnt, *scantmp;
     CK(da.get(&cnt, (size_t)M + 1));
     CK(da.get(&scantmp, ((size_t)M + 1 + 4095) / 4096 + 1));
@@ -577,6 +588,7 @@ int solve_direct(msp_instance *inst, const DirectPlan &dp, const Plan &kp, size_
   st.classes_done = c_end - c_begin;
   std::vector<std::vector<uint64_t>> out;
   uint32_t done = 0;
+  NvtxRange nv("msp direct: class joins and verification");
   const int rc =
       run_direct(lists, dp, c_begin, c_end, da, cp, prof, &st, inst->cancel, inst->first_only, &done, out);
   st.classes_done = done;

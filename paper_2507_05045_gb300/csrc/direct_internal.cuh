@@ -7,6 +7,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "checked.cuh"
+
 namespace msp {
 
 constexpr int kDirectThreads = 512;          // threads per join block
@@ -21,6 +23,22 @@ struct InnerGen {
   int q;                   // columns of the quarter
   int neg;                 // 1: store -K and -kappa (right inner list)
   uint32_t cmask;
+};
+
+// The outer quarter of one side of one instance (at most 9 columns): its
+// column tables and where its subset lists go.  Subset u's key is the sum of
+// its columns' keys (right side: kd minus it), its class likewise (masked),
+// its packed vector the sum of the packed columns, and its mask u.
+constexpr int kOuterColsMax = 9;
+struct OuterSeg {
+  uint32_t ck[kOuterColsMax];     // 32-bit key of each column
+  uint32_t cc[kOuterColsMax];     // class contribution of each column
+  uint64_t pc[kOuterColsMax][4];  // packed column vectors (16-bit row fields)
+  int q;                          // columns
+  int neg;                        // 1: key kd - K, class cd - kappa (right side)
+  uint32_t kd, cd, cmask;
+  uint32_t *okey, *ocls, *omask;  // [2^q]
+  uint64_t *ovec;                 // [2^q][4]
 };
 
 // The inner quarter of one side of one instance of a batch: its column
@@ -39,6 +57,7 @@ struct DirectSide {
   const uint32_t *ikey;  // [ni] inner keys, bucketed by class
   const uint32_t *ioff;  // [M + 1] bucket starts
   int no;
+  uint32_t ni;           // inner subsets (the bound of the MSP_CHECKED checks)
 };
 
 // One instance of a direct pass (device table: one entry for a single
@@ -122,6 +141,8 @@ cudaError_t launch_win(const WinBuild &w, bool place, cudaStream_t s);
 // Counts by class (scatter = false) or placement at the cursors of the
 // inner quarters of every segment of a batch (all of q columns).
 cudaError_t launch_direct_inner_batch(const InnerSeg *segs, int nseg, int q, bool scatter, cudaStream_t s);
+// Outer lists of nseg segments (device array), one block per segment.
+cudaError_t launch_direct_outer(const OuterSeg *segs, int nseg, cudaStream_t s);
 // Bucket starts of every segment of a batch (2^B <= 2^20): one block each.
 cudaError_t launch_direct_inner_offsets(const InnerSeg *segs, int nseg, uint32_t M, cudaStream_t s);
 // Class joins of a launch's classes [p.c0, p.c0 + p.nclass) of every instance.

@@ -83,7 +83,8 @@ static_assert(kBatch == 4, "a batch reads its bitmap words and bases as one uint
 
 template <typename F>
 __device__ __forceinline__ void group_records(uint32_t st, uint32_t len, uint32_t ka,
-                                              const uint32_t *__restrict__ ikey, uint2 *et_w, uint32_t *bm_w,
+                                              const uint32_t *__restrict__ ikey, uint32_t ni, uint2 *et_w,
+                                              uint32_t *bm_w,
                                               uint32_t *wb_w, uint32_t lo, uint32_t hi, F &&f) {
   const uint32_t ln = lane_id();
   const uint32_t ltmask = (1u << ln) - 1u;
@@ -133,12 +134,18 @@ __device__ __forceinline__ void group_records(uint32_t st, uint32_t len, uint32_
         const uint32_t word = wa[b];
         const uint32_t base = ba[b];
         const uint32_t k = i0 + 32u * b + ln;
-        const bool ok = k >= lo && k < send;
+        bool ok = k >= lo && k < send;
         const uint32_t c = base + __popc(word & lemask) - 1u;
+        if (ok && !MSP_IN_BOUNDS(c, 32u, 11u)) ok = false;  // compacted subset of the group
         const uint2 e = et_w[ok ? c : 0u];
         // lanes outside the range read inner element 0: every address
         // formed here lies inside the inner list
-        raw[b] = __ldg(ikey + (ok ? e.x + k : 0u));
+        uint32_t pos = ok ? e.x + k : 0u;
+        if (ok && !MSP_IN_BOUNDS(pos, ni, 12u)) {  // inner position of the record
+          ok = false;
+          pos = 0u;
+        }
+        raw[b] = __ldg(ikey + pos);
         ko[b] = e.y;
         okm |= static_cast<uint32_t>(ok) << b;
       }
@@ -282,7 +289,7 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
   // instance; bucket bounds [ioff[w], ioff[w + 1]) of it for a class (0, 0
   // past the outer list)
   const int el = wp * 32 + ln;
-  uint32_t kaL = 0, kaR = 0, clL = 0, clR = 0;
+  uint32_t kaL = 0, kaR = 0, clL = 0, clR = 0, niL = 0, niR = 0;
   uint32_t cur_inst = 0xffffffffu;
   uint32_t pfL0 = 0, pfL1 = 0, pfR0 = 0, pfR1 = 0;
   // carry: class r follows the previous class of the same work item, so a
@@ -322,6 +329,8 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
       ioffR = s_inst.side[1].ioff;
       ikeyL = s_inst.side[0].ikey;
       ikeyR = s_inst.side[1].ikey;
+      niL = s_inst.side[0].ni;
+      niR = s_inst.side[1].ni;
       kaL = el < noL ? s_inst.side[0].okey[el] : 0u;
       clL = el < noL ? s_inst.side[0].ocls[el] : 0u;
       kaR = el < noR ? s_inst.side[1].okey[el] : 0u;
@@ -383,7 +392,7 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
             lo = a > woff ? a - woff : 0u;
             hi = b > woff ? b - woff : 0u;
           }
-          group_records(stL, lnL, kaL, ikeyL, et_w, bm_w, wb_w, lo, hi,
+          group_records(stL, lnL, kaL, ikeyL, niL, et_w, bm_w, wb_w, lo, hi,
                         [&](uint32_t okm, const uint32_t(&key)[kBatch]) {
 #pragma unroll
             for (int b = 0; b < kBatch; ++b) {
@@ -408,7 +417,7 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
         __syncthreads();
         // ---- right records: probe ----
         if (wp * 32 < static_cast<uint32_t>(noR)) {
-          group_records(stR, lnR, kaR, ikeyR, et_w, bm_w, wb_w, 0u, 0xffffffffu,
+          group_records(stR, lnR, kaR, ikeyR, niR, et_w, bm_w, wb_w, 0u, 0xffffffffu,
                         [&](uint32_t okm, const uint32_t(&key)[kBatch]) {
             uint32_t fw[kBatch];
 #pragma unroll

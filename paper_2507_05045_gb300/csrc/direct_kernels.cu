@@ -121,6 +121,28 @@ __global__ void win_high_kernel(InnerGen g, int h, int hq, uint32_t *hkey, uint3
   hcls[H] = (g.neg ? 0u - cls : cls) & g.cmask;
 }
 
+// S1 for an outer quarter: one block per segment, one thread per subset,
+// which sums the tables of its columns.
+__global__ void __launch_bounds__(kOuterMax) direct_outer_kernel(const OuterSeg *segs) {
+  const OuterSeg &g = segs[blockIdx.x];
+  const uint32_t u = threadIdx.x;
+  if (u >= (1u << g.q)) return;
+  uint32_t key = 0, cls = 0;
+  uint64_t v[4] = {0, 0, 0, 0};
+  for (uint32_t b = u; b; b &= b - 1) {
+    const int j = __ffs(b) - 1;
+    key += g.ck[j];
+    cls += g.cc[j];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) v[w] += g.pc[j][w];
+  }
+  g.okey[u] = g.neg ? g.kd - key : key;
+  g.ocls[u] = (g.neg ? g.cd - cls : cls) & g.cmask;
+  g.omask[u] = u;
+#pragma unroll
+  for (int w = 0; w < 4; ++w) g.ovec[(size_t)u * 4 + w] = v[w];
+}
+
 template <bool kPlace>
 __global__ void __launch_bounds__(kWinThreads) win_kernel(WinBuild w) {
   extern __shared__ __align__(16) uint8_t wsm[];
@@ -165,8 +187,8 @@ __global__ void __launch_bounds__(kWinThreads) win_kernel(WinBuild w) {
         if (kPlace) {
           const uint32_t key = kH + e.x, mask = hm | e.y;
           if (staged) {
-            stage[pos] = make_uint2(key, mask);
-          } else {
+            if (MSP_IN_BOUNDS(pos, kWinCap, 31u)) stage[pos] = make_uint2(key, mask);  // stage slot
+          } else if (MSP_IN_BOUNDS(base + pos, 1ull << (w.h + w.hq), 32u)) {  // list position
             w.ikey[base + pos] = key;
             w.imask[base + pos] = mask;
           }
@@ -182,6 +204,7 @@ __global__ void __launch_bounds__(kWinThreads) win_kernel(WinBuild w) {
     for (uint32_t i = threadIdx.x; i < W; i += kWinThreads) w.cnt[w0 + i] = cur[i];
   } else if (staged) {
     for (uint32_t i = threadIdx.x; i < total; i += kWinThreads) {
+      if (!MSP_IN_BOUNDS(base + i, 1ull << (w.h + w.hq), 33u)) continue;  // list position
       const uint2 v = stage[i];
       w.ikey[base + i] = v.x;
       w.imask[base + i] = v.y;
@@ -202,6 +225,7 @@ __global__ void direct_inner_batch_kernel(const InnerSeg *segs, int c, uint64_t 
     if constexpr (kScatter) {
       walk_chunk(S.g, base, c, [&](uint32_t mask, uint32_t k, uint32_t r) {
         const uint32_t pos = atomicAdd(S.cnt + r, 1u);
+        if (!MSP_IN_BOUNDS(pos, 1ull << S.g.q, 34u)) return;  // list position
         S.ikey[pos] = k;
         S.imask[pos] = mask;
       });
@@ -307,7 +331,10 @@ __global__ void __launch_bounds__(kVT) direct_verify_kernel(DirectVerify v) {
       for (uint32_t j0 = b0[s]; j0 < b1[s]; j0 += 8) {
         uint32_t kk[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) kk[u] = j0 + u < b1[s] ? vi.side[s].ikey[j0 + u] : ~key;
+        for (int u = 0; u < 8; ++u) {
+          const bool in = j0 + u < b1[s] && MSP_IN_BOUNDS(j0 + u, vi.side[s].ni, 21u);  // bucket scan position
+          kk[u] = in ? vi.side[s].ikey[j0 + u] : ~key;
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           if (j0 + u < b1[s] && ka[s] + kk[u] == key) {
@@ -328,6 +355,10 @@ __global__ void __launch_bounds__(kVT) direct_verify_kernel(DirectVerify v) {
   const uint32_t np = nL * nR;
   for (uint32_t pi = threadIdx.x; pi < np; pi += kVT) {
     const uint2 l = cand[0][pi / nR], rr = cand[1][pi % nR];
+    if (!MSP_IN_BOUNDS(l.y, vi.side[0].ni, 22u) || !MSP_IN_BOUNDS(rr.y, vi.side[1].ni, 23u) ||
+        !MSP_IN_BOUNDS(l.x, static_cast<uint32_t>(vi.side[0].no), 24u) ||
+        !MSP_IN_BOUNDS(rr.x, static_cast<uint32_t>(vi.side[1].no), 25u))
+      continue;  // candidate positions inside the lists
     uint64_t vec[4];
     for (int w = 0; w < 4; ++w) vec[w] = vi.ovec[0][l.x * 4 + w] + vi.ovec[1][rr.x * 4 + w];
     const uint32_t mL = vi.imask[0][l.y], mR = vi.imask[1][rr.y];
@@ -395,6 +426,13 @@ cudaError_t launch_win_low(const InnerGen &g, int gshift, uint32_t *cnt_or_cur, 
 cudaError_t launch_win_high(const InnerGen &g, int h, int hq, uint32_t *hkey, uint32_t *hcls, cudaStream_t s) {
   const unsigned n = 1u << hq;
   win_high_kernel<<<(n + 255) / 256, 256, 0, s>>>(g, h, hq, hkey, hcls);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_direct_outer(const OuterSeg *segs, int nseg, cudaStream_t s) {
+  if (nseg < 1) return cudaSuccess;
+  static_assert((1 << kOuterColsMax) <= kOuterMax, "one thread per outer subset");
+  direct_outer_kernel<<<nseg, kOuterMax, 0, s>>>(segs);
   return cudaGetLastError();
 }
 

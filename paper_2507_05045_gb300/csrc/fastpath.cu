@@ -220,6 +220,7 @@ struct ScatterUnit {
   const uint32_t *ocls;
   const uint64_t *ikey;
   const uint32_t *ioff;
+  int64_t isize;  // inner list entries (the bound of the MSP_CHECKED checks)
   uint64_t *rec;
   uint32_t *fill;
   unsigned long long seg0;
@@ -270,6 +271,7 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
       u.ocls = g.ocls;
       u.ikey = g.ikey;
       u.ioff = g.ioff;
+      u.isize = g.isize;
       u.rec = side ? p.rec[1] : p.rec[0];
       u.fill = fi.fill[side] + (int64_t)cl * nd;
       u.seg0 = fi.class_base[side][cg_id];
@@ -403,14 +405,16 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
         for (int b = 0; b < kScPer; ++b) {
           const uint32_t K = K0 + b * 32;
           const uint32_t word = bm[K >> 5];
-          const uint32_t e = e_base + __popc(word & lemask) - 1u;
+          uint32_t e = e_base + __popc(word & lemask) - 1u;
           e_base += __popc(word);
           const uint32_t k = K + lanei;
+          if (k < n_round && !MSP_IN_BOUNDS(e, static_cast<uint32_t>(kScRound), 41u)) e = 0u;  // element
           rank[b] = e;  // element of the record until the rank replaces it
           // lanes past the round read inner element 0: every address formed
           // here is inside the inner list whether or not the load is
           // predicated
-          const uint32_t ii = k < n_round ? s_delta[e] + k : 0u;
+          uint32_t ii = k < n_round ? s_delta[e] + k : 0u;
+          if (!MSP_IN_BOUNDS(ii, static_cast<uint64_t>(u.isize), 42u)) ii = 0u;  // inner position
           keys[b] = __ldg(ikey + ii);
         }
 #pragma unroll
@@ -469,7 +473,10 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
 #pragma unroll
         for (int b = 0; b < kScPer; ++b) {
           const uint32_t k = K0 + b * 32 + lanei;
-          if (k < n_round) sorted[loff[digit_t<D>(keys[b])] + rank[b]] = keys[b];
+          if (k < n_round) {
+            const uint32_t sp = loff[digit_t<D>(keys[b])] + rank[b];
+            if (MSP_IN_BOUNDS(sp, static_cast<uint32_t>(kScRound), 43u)) sorted[sp] = keys[b];  // sorted slot
+          }
         }
       }
       {
@@ -704,7 +711,7 @@ __device__ __forceinline__ bool probe(uint64_t key, const uint64_t *__restrict__
   for (uint32_t j = 0; j < n; ++j) {
     if (fps[b * kJSlots + j] == fp) {
       const uint32_t idx = idxs[b * kJSlots + j];
-      if (idx < best && Lg[idx] == key) best = idx;
+      if (idx < best && MSP_IN_BOUNDS(idx, static_cast<uint32_t>(kFastCap), 44u) && Lg[idx] == key) best = idx;
     }
   }
   if (c > kJSlots) {

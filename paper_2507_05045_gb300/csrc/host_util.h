@@ -1,6 +1,7 @@
 // Host helpers shared by the solver translation units: a stream-ordered
 // device allocator that frees everything it handed out, the CUDA error
-// check that maps to msp_status codes, and per-launch event timing.
+// check that maps to msp_status codes, per-launch event timing and NVTX
+// ranges over the stages of a solve.
 #pragma once
 
 #include <algorithm>
@@ -8,6 +9,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "host_internal.h"
 
@@ -111,6 +113,38 @@ struct Prof {
     }
     for (auto e : pool) cudaEventDestroy(e);
   }
+};
+
+// A small ring of events (timing off) that bounds how many launches a
+// cancelable solve keeps queued: record after launch i, wait before launch
+// i + size.
+struct EventRing {
+  std::vector<cudaEvent_t> ev;
+  explicit EventRing(uint32_t n) : ev(n, nullptr) {
+    for (auto &e : ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  }
+  ~EventRing() {
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  EventRing(const EventRing &) = delete;
+  EventRing &operator=(const EventRing &) = delete;
+  cudaError_t record(uint32_t i, cudaStream_t s) { return cudaEventRecord(ev[i], s); }
+  cudaError_t wait(uint32_t i) { return cudaEventSynchronize(ev[i]); }
+};
+
+// NVTX range over a host stage of a solve (header-only NVTX3: with no
+// profiler attached a range costs a function call that does nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { end(); }
+  void end() {  // close the range before the end of the scope
+    if (open_) nvtxRangePop();
+    open_ = false;
+  }
+  bool open_ = true;
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 #define LAUNCH(kind, kernels, bytes, call) \

@@ -24,6 +24,8 @@
 // equal class can match, so classes are independent units of work.
 #pragma once
 
+#include "checked.cuh"
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -74,6 +76,7 @@ struct SideGen {
   int64_t osize;
   const uint64_t *ikey;
   const uint32_t *ioff;
+  int64_t isize;        // inner list entries (the bound of the MSP_CHECKED checks)
   int64_t slice_outer;  // outer elements per slice
   int slices;           // slices per class
   int wmax;             // outer elements per window of the streaming scatter

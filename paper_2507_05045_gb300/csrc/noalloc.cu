@@ -175,6 +175,7 @@ extern "C" int msp_solve_small_noalloc(const int32_t *A, const int32_t *d, int m
     g.ocls = o.cls;
     g.osize = o.size;
     g.ikey = in.key;
+    g.isize = in.size;
     g.ioff = in.off;
     const int64_t per_bucket = std::max<int64_t>(1, in.size / M);
     g.slice_outer = std::max<int64_t>(1, (int64_t(1) << 19) / per_bucket);

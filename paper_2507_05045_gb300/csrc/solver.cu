@@ -265,6 +265,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
   CK(h2d(d_ccol, ccol.data(), ccol.size() * 4));
 
   // ---- S1: quarter lists ----
+  NvtxRange nv_lists("msp: quarter lists and class buckets");
   QuarterDev qd[4];
   for (int k = 0; k < 4; ++k) {
     qd[k].q = p.q[k];
@@ -301,6 +302,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     LAUNCH(MSP_K_BUCKET, 1, 0, launch_bucket_scatter(q, mul[l], kadd[l], cadd[l], cmask, d_cursor, bd[l], s));
   }
 
+  nv_lists.end();
   // ---- row-1 candidate count C1 (the metric's unit of work) ----
   {
     int64_t qsum[4] = {0, 0, 0, 0};
@@ -338,6 +340,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     g.ocls = o.cls;
     g.osize = o.size;
     g.ikey = in.key;
+    g.isize = in.size;
     g.ioff = in.off;
     const int64_t per_bucket = std::max<int64_t>(1, in.size / M);
     g.slice_outer = std::max<int64_t>(1, (int64_t(1) << 19) / per_bucket);
@@ -750,10 +753,17 @@ int solve_instance(msp_instance *inst, uint64_t **masks, size_t *count, int *wor
   *masks = nullptr;
   *count = 0;
   if (words_per_mask) *words_per_mask = (inst->n + 63) / 64;
+  NvtxRange nv("msp_solve_all");
   if (cudaSetDevice(inst->device) != cudaSuccess) return fail(MSP_ECUDA, "cudaSetDevice failed");
   const auto t0 = std::chrono::steady_clock::now();
   SolveResult res;
   int rc = solve_impl(inst, &res);
+  if (kChecked) {  // MSP_CHECKED build: any failed bounds check fails the solve
+    const unsigned site = take_check_sites();
+    if (site)
+      return fail(MSP_ECUDA, "MSP_CHECKED: a bounds check failed at site " + std::to_string(site) +
+                                 " (the access was skipped)");
+  }
   if (rc != MSP_OK) {
     cudaStreamSynchronize(inst->stream);
     cudaGetLastError();
@@ -768,6 +778,26 @@ int solve_instance(msp_instance *inst, uint64_t **masks, size_t *count, int *wor
 
 // Device bytes a solve of an (m, n) instance needs for its quarter lists and
 // one residue pass of at least one class, capped at `cap` (0 = no cap).
+namespace {
+std::vector<CheckReader> &check_readers() {
+  static std::vector<CheckReader> r;
+  return r;
+}
+}  // namespace
+
+void register_check_reader(CheckReader r) { check_readers().push_back(r); }
+
+unsigned take_check_sites() {
+  if (!kChecked) return 0;
+  cudaDeviceSynchronize();
+  unsigned first = 0;
+  for (CheckReader r : check_readers()) {
+    const unsigned s = r();
+    if (s && !first) first = s;
+  }
+  return first;
+}
+
 size_t footprint_estimate(int m, int n, size_t cap) {
   {
     // the direct pass, when the instance fits it and its lists fit the cap
@@ -798,7 +828,9 @@ extern "C" {
 
 const char *msp_last_error(void) { return g_err.c_str(); }
 
-const char *msp_version(void) { return "libmsp 0.1 (sm_103a)"; }
+const char *msp_version(void) {
+  return msp::kChecked ? "libmsp 0.1 (sm_103a, MSP_CHECKED bounds checks)" : "libmsp 0.1 (sm_103a)";
+}
 
 int msp_plan(int m, int n, msp_plan_info *out) {
   if (!out) return fail(MSP_EINVAL, "out must be non-null");

@@ -87,8 +87,12 @@ def test_instance_budget_too_small(msp):
 
 
 def test_server_rejects_a_request_beyond_its_budget(msp):
+    # 170 MB: a (4,30) request needs about 160 MB (direct pass, with the
+    # match list and margin), an (8,70) one at least the streaming pass's
+    # 140 MB of reserves plus 38 MB of quarter lists
     A, d, _ = golden_8_70_plain()
-    with msp.Server(hbm_budget=64 << 20, max_inflight=1) as srv:
+    assert msp.plan_info(4, 30)["device_bytes"] <= 170 << 20
+    with msp.Server(hbm_budget=170 << 20, max_inflight=1) as srv:
         with pytest.raises(msp.MspError) as e:
             srv.submit(A, d)
         assert e.value.code == ENOMEM

@@ -70,3 +70,20 @@ def test_no_device_fails_loudly_without_cpu_fallback(lib):
     with pytest.raises(msp.MspError) as e:
         msp.solve_all(np.ones((1, 4), np.int32), [2])
     assert e.value.code == -4  # MSP_ECUDA
+
+
+def test_checked_build_loads_and_exports_every_symbol():
+    # the MSP_CHECKED variant of the library builds here (nvcc cross-compiles)
+    # and loads without a GPU; it is run on the parity cases by
+    # tests/test_gpu_checked.py
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2507_05045_gb300 import build, msp\n"
+            "lib = msp.load_library(build.build(checked=True))\n"
+            "print(lib.msp_version().decode())\n"
+            "print(all(hasattr(lib, s) for s in msp.EXPORTED_SYMBOLS))\n") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    version, exported = r.stdout.strip().splitlines()[-2:]
+    assert "MSP_CHECKED" in version and exported == "True"
