@@ -87,3 +87,19 @@ def test_checked_build_loads_and_exports_every_symbol():
     assert r.returncode == 0, r.stderr[-2000:]
     version, exported = r.stdout.strip().splitlines()[-2:]
     assert "MSP_CHECKED" in version and exported == "True"
+
+
+def test_surrogate_merged_rows_exceed_the_field_limit(lib):
+    # eq. 2 merges rows 1 and 2 with a multiplier above the row-1 sum; the
+    # merged (9,80) row reaches millions, past the 16-bit packed fields, so
+    # the library rejects the instance before any device work
+    import paper_2507_05045_gb300 as msp
+    import msp_instances as mi
+    A, d, _ = mi.generate(9, 80, 9080)
+    W = int(A[0].sum()) + 1
+    merged = A[0].astype(np.int64) + W * A[1].astype(np.int64)
+    A2 = np.vstack([merged, A[2:]]).astype(np.int32)
+    d2 = np.concatenate([[int(d[0]) + W * int(d[1])], d[2:]]).astype(np.int32)
+    with pytest.raises(msp.MspError) as e:
+        msp.Instance(A2, d2)
+    assert e.value.code == -2  # MSP_ERANGE
