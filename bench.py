@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--cols", "--n", dest="n", type=int, default=N_)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", choices=["9_80", "batch_6_50", "serving", "10_90_part", "profile_part",
-                                         "profile_small", "first_9_80", "k_sweep"],
+                                         "profile_small", "first_9_80", "k_sweep", "first_10_90"],
                     default="9_80",
                     help="9_80 (default): the headline exhaustive solve; batch_6_50: 64 (6,50) "
                          "instances in one batched call vs one at a time; serving: the mixed Poisson "
@@ -68,7 +68,9 @@ def parse():
                          "full-section captures; first_9_80: time to the first solution (the "
                          "quantity of the paper's tables) of the plain bench instance and of a "
                          "planted (9,80) instance; k_sweep: plain (8,70) and (9,80) instances with "
-                         "a_ij in [0, K) for K = 50, 100, 200 (the paper's (m, n, K) classes)")
+                         "a_ij in [0, K) for K = 50, 100, 200 (the paper's (m, n, K) classes); "
+                         "first_10_90: time to the first solution of a plain (10,90) instance on the "
+                         "streaming pass")
     ap.add_argument("--path", type=int, default=1, choices=[0, 1],
                     help="profile_part: 1 = direct pass, 0 = streaming pass")
     ap.add_argument("--requests", type=int, default=512)
@@ -660,6 +662,29 @@ def bench_first(args):
            "paper": "236.07 s average over four QOBLIB (9,80,100) instances, hybrid CPU+H200 (Table 1)"})
 
 
+def bench_first_10_90(args):
+    """Time to the first solution at (10,90) on the streaming pass (the
+    quantity of the paper's Table 1), for the plain instance of seed 1090:
+    the residue passes run in class order, the matches are verified after
+    every pass and the solve stops at the first pass that yields one."""
+    import paper_2507_05045_gb300 as msp
+    from paper_2507_05045_gb300 import build
+    build.build()
+    A, d, _ = mi.generate(10, 90, 1090)
+    with msp.Instance(A, d, first=True, profiling=True) as inst:
+        t0 = time.perf_counter()
+        sols = inst.solve_all()
+        dt = time.perf_counter() - t0
+        st = inst.stats()
+    _emit({"metric": "time to first solution at (10,90)", "value": dt, "unit": "s", "n_gpus": 1, "steps": 1,
+           "warmup": 0, "higher_is_better": False, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": "(10,90) plain instance seed 1090, a_ij in [0,99], streaming pass, stop after "
+                                  "the first residue pass that yields a solution", "path": st["path"]},
+           "solutions_found": len(sols), "classes_done": st["classes_done"], "classes_total": st["classes_total"],
+           "records_done": st["records_done"], "passes": st["passes"], "kernels": st["kernels"],
+           "paper": "148 663 s average over four QOBLIB (10,90,100) instances, hybrid CPU+H200 (Table 1)"})
+
+
 def bench_k_sweep(args):
     """The coefficient range K of the paper's (m, n, K) classes (Table 1):
     plain (8,70) and (9,80) instances with a_ij in [0, K) for K in
@@ -717,6 +742,9 @@ def main():
         elif args.config == "first_9_80":
             if rank == 0:
                 bench_first(args)
+        elif args.config == "first_10_90":
+            if rank == 0:
+                bench_first_10_90(args)
         elif args.config == "k_sweep":
             if rank == 0:
                 bench_k_sweep(args)

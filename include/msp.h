@@ -178,12 +178,16 @@ MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
  *                        classes are joined in launches of about 2^32
  *                        records, the matches verified after each, and the
  *                        solve stops after the first launch that yields a
- *                        solution.  The result is then a nonempty subset of
- *                        the solutions (all of those found so far) and
- *                        msp_stats.classes_done counts the classes joined;
- *                        an instance with no solution is still searched to
- *                        the end.  0 = every solution (default).  The
- *                        streaming and exact passes ignore it. */
+ *                        solution.  The streaming pass likewise verifies the
+ *                        matches after every residue pass and stops after
+ *                        the first pass that yields a solution (the exact
+ *                        re-runs of overflowed passes come only after all
+ *                        streaming passes).  The result is then a nonempty
+ *                        subset of the solutions (all of those found so far)
+ *                        and msp_stats.classes_done counts the classes
+ *                        joined; an instance with no solution is still
+ *                        searched to the end.  0 = every solution
+ *                        (default). */
 enum {
   MSP_OPT_EXACT_PATH = 1,
   MSP_OPT_CLASS_PART = 2,

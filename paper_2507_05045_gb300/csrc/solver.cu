@@ -361,6 +361,85 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
   CK(da.get(&match_count, 1));
   CK(cudaMemsetAsync(match_count, 0, sizeof(unsigned long long), s));
 
+  // ---- S6: recovery and exact verification of the matches [m0, m1);
+  //      solutions are appended to res (two words each) ----
+  uint64_t verified_to = 0;
+  auto verify_matches = [&](uint64_t m0, uint64_t m1) -> int {
+    const uint64_t nm = m1 - m0;
+    RecoverDev rd{};
+    rd.match_key = match_key + m0;
+    rd.match_cls = match_cls + m0;
+    rd.nmatch = nm;
+    rd.side[0] = gens[0];
+    rd.side[1] = gens[1];
+    rd.oidx[0] = bd[0].idx;
+    rd.iidx[0] = bd[1].idx;
+    rd.oidx[1] = bd[2].idx;
+    rd.iidx[1] = bd[3].idx;
+    rd.cmask = cmask;
+    unsigned long long *tmp64;
+    CK(da.get(&tmp64, (nm + 1 + 4095) / 4096 + 1));
+    for (int side = 0; side < 2; ++side) {
+      CK(da.get(&rd.cand_count[side], nm));
+      CK(da.get(&rd.cand_off[side], nm + 1));
+      CK(da.get(&rd.cand_cur[side], nm));
+      CK(cudaMemsetAsync(rd.cand_count[side], 0, sizeof(unsigned long long) * nm, s));
+      CK(cudaMemsetAsync(rd.cand_cur[side], 0, sizeof(unsigned long long) * nm, s));
+    }
+    LAUNCH(MSP_K_RECOVER, 2, 0, launch_recover(rd, false, s));
+    unsigned long long ncand[2];
+    for (int side = 0; side < 2; ++side) {
+      LAUNCH(MSP_K_RECOVER, 3, 0, launch_scan_u64(rd.cand_count[side], rd.cand_off[side], nm, tmp64, s));
+      CK(d2h(&ncand[side], rd.cand_off[side] + nm, sizeof(unsigned long long)));
+    }
+    CK(cudaStreamSynchronize(s));
+    for (int side = 0; side < 2; ++side) {
+      rd.cand_cap[side] = ncand[side];
+      CK(da.get(&rd.cand[side], ncand[side]));
+    }
+    CK(da.get(&rd.cand_match[0], ncand[0]));
+    LAUNCH(MSP_K_RECOVER, 2, 0, launch_recover(rd, true, s));
+
+    VerifyDev vd{};
+    vd.ic = ic;
+    for (int k = 0; k < 4; ++k) {
+      vd.qvec[k] = qd[k].vec;
+      vd.qsize[k] = qd[k].size;
+    }
+    vd.candL = rd.cand[0];
+    vd.candL_match = rd.cand_match[0];
+    vd.nL = ncand[0];
+    vd.candR = rd.cand[1];
+    vd.candR_off = rd.cand_off[1];
+    unsigned long long *cnts;
+    CK(da.get(&cnts, 2));
+    vd.sol_count = cnts;
+    vd.pairs_checked = cnts + 1;
+    uint64_t cap = 1u << 16;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      CK(da.get(&vd.sol, 2 * cap));
+      vd.sol_cap = cap;
+      CK(cudaMemsetAsync(cnts, 0, 2 * sizeof(unsigned long long), s));
+      LAUNCH(MSP_K_VERIFY, vd.nL ? 1 : 0, 0, launch_verify(vd, s));
+      unsigned long long hc[2];
+      CK(d2h(hc, cnts, sizeof(hc)));
+      CK(cudaStreamSynchronize(s));
+      if (hc[0] <= cap) {
+        st.pairs_verified += hc[1];
+        const size_t at = res->masks.size();
+        res->masks.resize(at + 2 * hc[0]);
+        if (hc[0]) {
+          CK(d2h(res->masks.data() + at, vd.sol, sizeof(uint64_t) * 2 * hc[0]));
+          CK(cudaStreamSynchronize(s));
+        }
+        return MSP_OK;
+      }
+      if (hc[0] > (1ull << 28)) return fail(MSP_EOVERFLOW, "more than 2^28 solutions");
+      cap = hc[0];
+    }
+    return MSP_OK;
+  };
+
   uint64_t *rec[2] = {nullptr, nullptr};
   uint64_t rec_cap[2] = {0, 0};
   // (re)allocate the record buffers to hold at least need[] records
@@ -384,6 +463,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
   st.classes_done = c_end - c_begin;
   int passes = 0;
   uint64_t oversize = 0;
+  bool found_first = false;  // time to first: a pass yielded a solution, the rest is skipped
   std::vector<std::pair<uint32_t, uint32_t>> exact_ranges;
   bool fast = !inst->force_exact && c_begin < c_end;
   std::vector<unsigned long long> csz[2];
@@ -508,6 +588,9 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     fp.match_cls = match_cls;
     fp.match_count = match_count;
     fp.match_cap = match_cap;
+    uint64_t recs_run = 0;
+    uint32_t classes_run = 0;
+    size_t passes_run = 0;
     for (size_t k = 0; k < plan.size(); ++k) {
       if (inst->cancel && *inst->cancel) return fail(MSP_ECANCELED, "request canceled");
       const PassPlan &pp = plan[k];
@@ -520,6 +603,36 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
       LAUNCH(MSP_K_GEN_SCATTER, 1, 8 * pp.recs, launch_scatter_fast(fp, run, s));
       LAUNCH(MSP_K_JOIN, 1, 8 * pp.recs, launch_join_fast(fp, run, s));
       ++passes;
+      ++passes_run;
+      recs_run += pp.recs;
+      classes_run += static_cast<uint32_t>(run);
+      if (inst->first_only) {
+        // time to first: verify this pass's new matches and stop at the
+        // first pass that yields a solution (a pass whose partitions
+        // overflowed may have missed matches; it is re-run exactly below
+        // unless a solution turns up first)
+        unsigned int err1 = 0;
+        unsigned long long nm = 0;
+        CK(d2h(&err1, d_err, sizeof(err1)));
+        CK(d2h(&nm, match_count, sizeof(nm)));
+        CK(cudaStreamSynchronize(s));
+        prof.flush();
+        if (err1) return fail(MSP_ETIMEDOUT, "a bulk copy did not complete within its time limit");
+        if (nm > match_cap) return fail(MSP_EOVERFLOW, "more than 2^20 matched keys");
+        if (nm > verified_to) {
+          const int rc = verify_matches(verified_to, nm);
+          if (rc != MSP_OK) return rc;
+          verified_to = nm;
+        }
+        if (!res->masks.empty()) {
+          found_first = true;
+          break;
+        }
+      }
+    }
+    if (found_first) {
+      st.classes_done = classes_run;
+      st.records_done = recs_run;
     }
     std::vector<unsigned int> ovf_h(plan.size());
     unsigned int err_h = 0;
@@ -528,7 +641,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     CK(cudaStreamSynchronize(s));
     prof.flush();
     if (err_h) return fail(MSP_ETIMEDOUT, "a bulk copy did not complete within its time limit");
-    for (size_t k = 0; k < plan.size(); ++k)
+    for (size_t k = 0; k < passes_run && !found_first; ++k)
       if (ovf_h[k]) {
         exact_ranges.push_back({plan[k].c0, plan[k].c1});
         ++st.fast_passes_redone;
@@ -537,7 +650,7 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     exact_ranges.push_back({c_begin, c_end});
   }
 
-  if (!exact_ranges.empty()) {
+  if (!exact_ranges.empty() && !found_first) {
     const int nd = 1 << p.Dx;  // exact pass digits
     // ---- exact passes: count, offsets, scatter, shared-memory join; any
     //      partition larger than shared memory goes to join_big ----
@@ -642,78 +755,9 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
   st.key_matches = nmatch;
   if (nmatch > match_cap) return fail(MSP_EOVERFLOW, "more than 2^20 matched keys");
 
-  if (nmatch > 0) {
-    // ---- S6: recovery and exact verification ----
-    RecoverDev rd{};
-    rd.match_key = match_key;
-    rd.match_cls = match_cls;
-    rd.nmatch = nmatch;
-    rd.side[0] = gens[0];
-    rd.side[1] = gens[1];
-    rd.oidx[0] = bd[0].idx;
-    rd.iidx[0] = bd[1].idx;
-    rd.oidx[1] = bd[2].idx;
-    rd.iidx[1] = bd[3].idx;
-    rd.cmask = cmask;
-    unsigned long long *tmp64;
-    CK(da.get(&tmp64, (nmatch + 1 + 4095) / 4096 + 1));
-    for (int side = 0; side < 2; ++side) {
-      CK(da.get(&rd.cand_count[side], nmatch));
-      CK(da.get(&rd.cand_off[side], nmatch + 1));
-      CK(da.get(&rd.cand_cur[side], nmatch));
-      CK(cudaMemsetAsync(rd.cand_count[side], 0, sizeof(unsigned long long) * nmatch, s));
-      CK(cudaMemsetAsync(rd.cand_cur[side], 0, sizeof(unsigned long long) * nmatch, s));
-    }
-    LAUNCH(MSP_K_RECOVER, 2, 0, launch_recover(rd, false, s));
-    unsigned long long ncand[2];
-    for (int side = 0; side < 2; ++side) {
-      LAUNCH(MSP_K_RECOVER, 3, 0, launch_scan_u64(rd.cand_count[side], rd.cand_off[side], nmatch, tmp64, s));
-      CK(d2h(&ncand[side], rd.cand_off[side] + nmatch, sizeof(unsigned long long)));
-    }
-    CK(cudaStreamSynchronize(s));
-    for (int side = 0; side < 2; ++side) {
-      rd.cand_cap[side] = ncand[side];
-      CK(da.get(&rd.cand[side], ncand[side]));
-    }
-    CK(da.get(&rd.cand_match[0], ncand[0]));
-    LAUNCH(MSP_K_RECOVER, 2, 0, launch_recover(rd, true, s));
-
-    VerifyDev vd{};
-    vd.ic = ic;
-    for (int k = 0; k < 4; ++k) {
-      vd.qvec[k] = qd[k].vec;
-      vd.qsize[k] = qd[k].size;
-    }
-    vd.candL = rd.cand[0];
-    vd.candL_match = rd.cand_match[0];
-    vd.nL = ncand[0];
-    vd.candR = rd.cand[1];
-    vd.candR_off = rd.cand_off[1];
-    unsigned long long *cnts;
-    CK(da.get(&cnts, 2));
-    vd.sol_count = cnts;
-    vd.pairs_checked = cnts + 1;
-    uint64_t cap = 1u << 16;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      CK(da.get(&vd.sol, 2 * cap));
-      vd.sol_cap = cap;
-      CK(cudaMemsetAsync(cnts, 0, 2 * sizeof(unsigned long long), s));
-      LAUNCH(MSP_K_VERIFY, vd.nL ? 1 : 0, 0, launch_verify(vd, s));
-      unsigned long long hc[2];
-      CK(d2h(hc, cnts, sizeof(hc)));
-      CK(cudaStreamSynchronize(s));
-      st.pairs_verified = hc[1];
-      if (hc[0] <= cap) {
-        res->masks.resize(2 * hc[0]);
-        if (hc[0]) {
-          CK(d2h(res->masks.data(), vd.sol, sizeof(uint64_t) * 2 * hc[0]));
-          CK(cudaStreamSynchronize(s));
-        }
-        break;
-      }
-      if (hc[0] > (1ull << 28)) return fail(MSP_EOVERFLOW, "more than 2^28 solutions");
-      cap = hc[0];
-    }
+  if (nmatch > verified_to && !found_first) {
+    const int rc = verify_matches(verified_to, nmatch);
+    if (rc != MSP_OK) return rc;
   }
   st.device_bytes = da.peak;
   da.release();

@@ -483,6 +483,26 @@ def test_streaming_pass_with_large_inner_quarters(msp):
         assert solve(msp, A2, d2.astype(np.int32), {"direct": 1})[0] == want
 
 
+def test_first_solution_mode_streaming_pass(msp):
+    # the streaming pass verifies after every residue pass and stops at the
+    # first one that yields a solution: a nonempty subset of the oracle's set
+    for e, A, d, x, sols in load_golden("sols_8_70.json"):
+        with msp.Instance(A, d, plan={"direct": 0}, first=True, memory_budget=4 << 30) as inst:
+            got = inst.solve_all()
+            st = inst.stats()
+        assert st["path"] == "streaming"
+        assert got and set(got) <= set(sols), e["planted"]
+        assert 0 < st["classes_done"] <= st["classes_total"]
+    for e, A, d, x, sols in load_golden("sols_6_50_batch.json")[:3]:
+        with msp.Instance(A, d, plan={"direct": 0}, first=True) as inst:
+            got = inst.solve_all()
+            st = inst.stats()
+        if not sols:
+            assert got == [] and st["classes_done"] == st["classes_total"]
+        else:
+            assert got and set(got) <= set(sols)
+
+
 def test_first_solution_mode(msp):
     # time-to-first: a nonempty subset of the oracle's full solution set,
     # found before all classes are joined; an instance without solutions is
