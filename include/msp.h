@@ -146,14 +146,15 @@ MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
  *                       is the full solution set, so parts can be solved by
  *                       different processes or GPUs, or one part timed to
  *                       project the full time (records_done / all records). */
-/*   MSP_OPT_CLASS_BITS   residue classes 2^B of the plan, B in [0, 23]
+/*   MSP_OPT_CLASS_BITS   residue classes 2^B of the plan, B in [0, 27]
  *   MSP_OPT_DIGIT_BITS   radix digit bits D of the streaming pass, in [0, 12]
  *                        (partitions of about |L| / 2^(B + D) records; a class
  *                        whose partitions would not fit shared memory is
  *                        solved on the exact path)
  *   MSP_OPT_INNER_BITS   the inner quarter of each side (Q3 of L, Q4 of R)
- *                        gets B + value columns (at most 27, never fewer than
- *                        the even split), so an inner residue bucket holds
+ *                        gets B + value columns (at most 27, or 30 when B is
+ *                        above 23; never fewer than the even split), so an
+ *                        inner residue bucket holds
  *                        about 2^value elements: the run of records one outer
  *                        element expands to in the scatter, in [0, 12]
  *                        For these three, -1 (the default) restores the

@@ -36,6 +36,7 @@ _PER_CLASS = ("gen_count", "offsets", "gen_scatter", "join", "join_big", "other"
               "verify")
 _PER_SOLVE = ("gray", "bucket", "c1")
 STREAM_KEYS = ("class_bits", "digit_bits", "inner_bits")
+MAX_CLASS_BITS = 27  # MSP_OPT_CLASS_BITS range of the library
 
 
 def cache_path() -> str:
@@ -98,7 +99,7 @@ def candidates(base: dict, lg: int, direct: bool = True) -> list[dict]:
     out = [{"direct": 1, "table_bits": tb} for tb in (14, 13, 15)] if direct else []
     out.append(dict(base, direct=0))
     for B in (B0 - 1, B0, B0 + 1):
-        if B < 0 or B > 23:
+        if B < 0 or B > MAX_CLASS_BITS:
             continue
         for part_bits in (12, 11):
             D = lg - B - part_bits

@@ -240,8 +240,11 @@ int solve_batch_impl(const int32_t *const *A, const int32_t *const *d, int m, in
       g.slice_outer = std::max<int64_t>(1, (int64_t(1) << 19) / per_bucket);
       g.slices = static_cast<int>((o.size + g.slice_outer - 1) / g.slice_outer);
       g.wmax = scatter_window(in.size, M);
-      CK(launch_class_sizes(side == 0 ? it.bd[0].off : it.bd[2].off, side == 0 ? it.bd[1].off : it.bd[3].off, M, 0,
-                            M, d_csz + ((size_t)t * 2 + side) * M, s));
+      unsigned long long *dst = d_csz + ((size_t)t * 2 + side) * M;
+      if (o.size < (int64_t)M)  // fewer outer elements than classes: sum over the elements
+        CK(launch_class_sizes_elems(o.cls, o.size, in.off, M, 0, M, dst, s));
+      else
+        CK(launch_class_sizes(o.off, in.off, M, 0, M, dst, s));
     }
   }
   std::vector<unsigned long long> csz_all((size_t)K * 2 * M);

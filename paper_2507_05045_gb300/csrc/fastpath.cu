@@ -151,6 +151,44 @@ __global__ void __launch_bounds__(kCsR) class_size_kernel(const uint32_t *__rest
   (void)r;
 }
 
+// The same sizes from the outer elements themselves, for an outer list of
+// fewer elements than classes: out[r] = sum over elements e of
+// n_I[(r - class(e)) mod M].  A block owns kCsR consecutive r (so a warp's
+// bucket loads are contiguous) and walks the elements' classes in tiles
+// staged in shared memory.  Work: elements x classes of the range.
+constexpr int kCsE = 2048;
+
+__global__ void __launch_bounds__(kCsR) class_size_elems_kernel(const uint32_t *__restrict__ ocls, int64_t no,
+                                                                const uint32_t *__restrict__ offI, uint32_t M,
+                                                                uint32_t rbeg, uint32_t rcount,
+                                                                unsigned long long *out) {
+  __shared__ uint32_t sc[kCsE];
+  const uint32_t ri = blockIdx.x * kCsR + threadIdx.x;
+  const uint32_t r = rbeg + ri;
+  const uint32_t mask = M - 1u;
+  unsigned long long acc = 0;
+  for (int64_t e0 = 0; e0 < no; e0 += kCsE) {
+    const int ne = static_cast<int>(min(static_cast<int64_t>(kCsE), no - e0));
+    for (int i = threadIdx.x; i < ne; i += kCsR) sc[i] = ocls[e0 + i];
+    __syncthreads();
+    if (ri < rcount)
+      for (int i = 0; i < ne; ++i) {
+        const uint32_t w = (r - sc[i]) & mask;
+        acc += offI[w + 1] - offI[w];
+      }
+    __syncthreads();
+  }
+  if (ri < rcount) out[ri] = acc;
+}
+
+cudaError_t launch_class_sizes_elems(const uint32_t *ocls, int64_t no, const uint32_t *offI, uint32_t M,
+                                     uint32_t rbeg, uint32_t rcount, unsigned long long *out, cudaStream_t s) {
+  if (rcount == 0) return cudaSuccess;
+  const uint32_t blocks = (rcount + kCsR - 1) / kCsR;
+  class_size_elems_kernel<<<blocks, kCsR, 0, s>>>(ocls, no, offI, M, rbeg, rcount, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_class_sizes(const uint32_t *offO, const uint32_t *offI, uint32_t M, uint32_t rbeg,
                                uint32_t rcount, unsigned long long *out, cudaStream_t s) {
   if (rcount == 0) return cudaSuccess;

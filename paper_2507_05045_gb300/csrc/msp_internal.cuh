@@ -34,6 +34,7 @@ namespace msp {
 constexpr int kMaxRows = 16;      // 16-bit fields, 4 per 64-bit word
 constexpr int kMaxVecWords = 4;
 constexpr int kMaxN = 100;
+constexpr int kMaxStreamClassBits = 27;  // residue classes of the streaming and exact passes
 constexpr int kMaskWords = 2;     // n <= 128 fits two words
 constexpr int kMaxClassRows = 4;
 
@@ -138,6 +139,9 @@ struct FastPass {
   uint64_t match_cap;
 };
 // out[i] = exact size of class rbeg + i, i < rcount (classes mod M).
+// The same from the classes of the no outer elements (cheaper when no < M).
+cudaError_t launch_class_sizes_elems(const uint32_t *ocls, int64_t no, const uint32_t *offI, uint32_t M,
+                                     uint32_t rbeg, uint32_t rcount, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_class_sizes(const uint32_t *offO, const uint32_t *offI, uint32_t M, uint32_t rbeg,
                                uint32_t rcount, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_scatter_fast(const FastPass &p, int nclass_run, cudaStream_t s);

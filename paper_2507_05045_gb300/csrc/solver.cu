@@ -49,8 +49,11 @@ Plan make_plan(int m, int n, const PlanChoice &ch) {
   p.lgL = p.q[0] + p.q[2];
   p.lgR = p.q[1] + p.q[3];
   const int lgmax = std::max(p.lgL, p.lgR);
-  // about 2^21 records per class and side (at most 2^23 classes)
-  p.B = ch.B >= 0 ? std::min(23, ch.B) : std::min(23, std::max(0, lgmax - 21));
+  // about 2^21 records per class and side (at most 2^23 classes); halves too
+  // large for partitions of at most 2^12 records at 2^23 classes and a
+  // 12-bit digit (n >= 96) take up to 2^27 classes of 2^(lgmax - B) records
+  p.B = ch.B >= 0 ? std::min(kMaxStreamClassBits, ch.B) : std::min(23, std::max(0, lgmax - 21));
+  if (ch.B < 0 && lgmax - p.B - 12 > 12) p.B = std::min(kMaxStreamClassBits, lgmax - 24);
   // row 1 alone while its residues stay uniform (2^B <= 256 against a
   // row-1 spread of a few hundred); three rows beyond, which keeps the class
   // sizes within about one percent of each other (four rows past 2^18
@@ -59,13 +62,16 @@ Plan make_plan(int m, int n, const PlanChoice &ch) {
   p.t = std::min(p.t, m);
   // Uneven halves: the inner quarter of each side (Q3 of L, Q4 of R) takes
   // columns from the outer one until an inner residue bucket holds about 16
-  // elements (2^(q_inner - B)), at most 2^27 of them, so that every outer
-  // element of a scatter window expands to a run of consecutive inner keys.
-  // |L| and |R| do not change, nor do the classes and partitions.
+  // elements (2^(q_inner - B)), at most 2^27 of them (2^30 for the plans of
+  // more than 2^23 classes, whose lists then take about 120 GB), so that
+  // every outer element of a scatter window expands to a run of consecutive
+  // inner keys.  |L| and |R| do not change, nor do the classes and
+  // partitions.
   const int inner_bits = ch.inner >= 0 ? ch.inner : 4;
+  const int inner_cap = p.B > 23 ? 30 : 27;
   for (int side = 0; side < 2; ++side) {
     const int tot = p.q[side] + p.q[side + 2];
-    const int want = std::min({std::max(p.q[side + 2], p.B + inner_bits), 27, tot - 1});
+    const int want = std::min({std::max(p.q[side + 2], p.B + inner_bits), inner_cap, tot - 1});
     if (want > p.q[side + 2]) {
       p.q[side + 2] = want;
       p.q[side] = tot - want;
@@ -474,8 +480,18 @@ int solve_impl(msp_instance *inst, SolveResult *res) {
     const uint32_t ncl = c_end - c_begin;
     unsigned long long *d_csz;
     CK(da.get(&d_csz, 2 * (size_t)ncl));
-    LAUNCH(MSP_K_OTHER, 1, 0, launch_class_sizes(bd[0].off, bd[1].off, M, c_begin, ncl, d_csz, s));
-    LAUNCH(MSP_K_OTHER, 1, 0, launch_class_sizes(bd[2].off, bd[3].off, M, c_begin, ncl, d_csz + ncl, s));
+    // the cheaper form: over the M outer buckets, or over the outer elements
+    // when they are fewer (many classes, e.g. the n = 100 plans)
+    for (int side = 0; side < 2; ++side) {
+      const BucketDev &o = bd[side == 0 ? 0 : 2];
+      const BucketDev &in = bd[side == 0 ? 1 : 3];
+      if (o.size < (int64_t)M) {
+        LAUNCH(MSP_K_OTHER, 1, 0,
+               launch_class_sizes_elems(o.cls, o.size, in.off, M, c_begin, ncl, d_csz + (size_t)side * ncl, s));
+      } else {
+        LAUNCH(MSP_K_OTHER, 1, 0, launch_class_sizes(o.off, in.off, M, c_begin, ncl, d_csz + (size_t)side * ncl, s));
+      }
+    }
     for (int side = 0; side < 2; ++side) {
       csz[side].assign(M, 0);
       capv[side].assign(M, 0);
@@ -987,7 +1003,7 @@ int msp_set_option(msp_instance *inst, int option, int64_t value) {
       inst->parts = value;
       return MSP_OK;
     case MSP_OPT_CLASS_BITS:
-      if (value < -1 || value > 23) return fail(MSP_ERANGE, "class bits must lie in [-1, 23]");
+      if (value < -1 || value > kMaxStreamClassBits) return fail(MSP_ERANGE, "class bits must lie in [-1, 27]");
       inst->plan_B = static_cast<int>(value);
       return MSP_OK;
     case MSP_OPT_DIGIT_BITS:

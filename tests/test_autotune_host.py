@@ -19,7 +19,7 @@ def test_candidates_start_with_the_formula_plan_and_are_distinct():
     for c in cands[3:]:
         assert set(c) == set(autotune.STREAM_KEYS) | {"direct"} and c["direct"] == 0
         assert set(c) <= set(msp.PLAN_KEYS)
-        assert 0 <= c["class_bits"] <= 23 and 0 <= c["digit_bits"] <= 12
+        assert 0 <= c["class_bits"] <= 27 and 0 <= c["digit_bits"] <= 12
         assert abs(c["class_bits"] - 19) <= 1
         # partitions of 2^11 .. 2^12 records: inside the streaming join's capacity
         if c is not cands[3]:
@@ -29,9 +29,9 @@ def test_candidates_start_with_the_formula_plan_and_are_distinct():
 
 
 def test_candidates_respect_the_bounds():
-    for lg, B0, D0 in [(15, 0, 3), (50, 23, 12), (1, 0, 0)]:
+    for lg, B0, D0 in [(15, 0, 3), (50, 23, 12), (50, 27, 12), (1, 0, 0)]:
         for c in autotune.candidates({"class_bits": B0, "digit_bits": D0, "inner_bits": 4}, lg, False):
-            assert 0 <= c["class_bits"] <= 23
+            assert 0 <= c["class_bits"] <= 27
             assert 0 <= c["digit_bits"] <= 12
 
 

@@ -483,6 +483,21 @@ def test_streaming_pass_with_large_inner_quarters(msp):
         assert solve(msp, A2, d2.astype(np.int32), {"direct": 1})[0] == want
 
 
+def test_streaming_pass_with_many_classes(msp):
+    # the plans of n >= 96 take up to 2^27 residue classes, whose exact sizes
+    # come from the outer elements (fewer than the classes); forced here on
+    # the (8,70) instances (2^24 classes of 2^11 records) and a (6,50) one
+    # (2^27 classes, most of them empty) against the oracle's full sets
+    for e, A, d, x, sols in load_golden("sols_8_70.json"):
+        got, st = solve(msp, A, d, {"class_bits": 24, "digit_bits": 0, "direct": 0})
+        assert st["class_bits"] == 24 and st["classes_total"] == 1 << 24
+        assert got == sols, e["planted"]
+    for e, A, d, x, sols in load_golden("sols_6_50_batch.json")[32:34]:
+        got, st = solve(msp, A, d, {"class_bits": 27, "digit_bits": 0, "direct": 0})
+        assert st["class_bits"] == 27
+        assert got == sols, e["seed"]
+
+
 def test_first_solution_mode_streaming_pass(msp):
     # the streaming pass verifies after every residue pass and stops at the
     # first one that yields a solution: a nonempty subset of the oracle's set
@@ -530,7 +545,7 @@ def test_first_solution_mode(msp):
 
 def test_plan_options_are_validated(msp):
     A, d, _ = mi.generate(4, 30, 1)
-    for bad in [{"class_bits": 24}, {"digit_bits": 13}, {"inner_bits": -2}, {"table_bits": 16},
+    for bad in [{"class_bits": 28}, {"digit_bits": 13}, {"inner_bits": -2}, {"table_bits": 16},
                 {"table_bits": 11}, {"direct": 2}]:
         with pytest.raises(msp.MspError) as e:
             msp.Instance(A, d, plan=bad)
