@@ -4,8 +4,8 @@ The expected plans follow the formulas of the two passes: the direct pass
 splits each half into an outer quarter of at most 9 columns and an inner
 quarter of B + 4 columns, B = max(0, log2 |half| - 13), whenever both halves
 have at most 40 columns; otherwise the streaming pass takes
-B = min(23, log2 |half| - 21) classes (raised to min(27, log2 |half| - 24)
-when partitions at 2^23 classes and 12 digit bits would pass 2^12 records),
+B = min(23, log2 |half| - 21) classes (min(27, log2 |half| - 20) for halves
+of 44 columns or more),
 inner quarters of B + 4 columns (at most 27, or 30 past 2^23 classes) and
 D = min(12, log2 |half| - B - 12) digit bits.
 """
@@ -32,7 +32,7 @@ def test_headline_shapes():
 
     p = msp.plan_info(10, 90)
     assert (p["path"], p["class_bits"], p["class_rows"], p["quarter"], p["digit_bits"]) == \
-        ("streaming", 23, 4, [18, 18, 27, 27], 10)
+        ("streaming", 25, 4, [16, 16, 29, 29], 8)
     assert p["records_left"] == p["records_right"] == 1 << 45
 
     p = msp.plan_info(4, 30)
@@ -61,8 +61,8 @@ def test_every_shape(m):
             assert p["path"] == "streaming"
             lg = max(q[0] + q[2], q[1] + q[3])
             B = min(23, max(0, lg - 21))
-            if lg - B - 12 > 12:
-                B = min(27, lg - 24)
+            if lg >= 44:
+                B = min(27, lg - 20)
             assert p["class_bits"] == B
             assert p["digit_bits"] == min(12, max(0, lg - B - 12))
             assert max(q[2], q[3]) <= (30 if B > 23 else 27)
