@@ -10,7 +10,8 @@ repository root:
 ``--only 8_70`` writes the (8,70) instance of seed 8, plain and planted, in
 full with the four-list oracle (minutes of CPU); ``--only 9_80`` writes the
 plain (9,80) instance of seed 9080 in full (the benchmark instance; about two
-hours on 8 cores).  Those runs go slice range by slice range and keep their
+hours on 8 cores); ``--only 9_80_planted`` the planted (9,80) instance of
+seed 9 (40 ones) likewise.  Those runs go slice range by slice range and keep their
 progress in a state file beside the output (``--state``), so an interrupted
 run resumes where it stopped.
 Each output file holds, per instance, the generator arguments and the sorted
@@ -161,6 +162,9 @@ def main():
         write("sols_10_70_subcube.json", [entry_10_70_subcube(state)], "oracle.fourlist")
     if args.only == "7_60_more":
         write("sols_7_60_more.json", entries_7_60_with_solutions(3, 70), "oracle.fourlist")
+    if args.only == "9_80_planted":
+        state = args.state or os.path.join(HERE, "sols_9_80_planted.state.json")
+        write("sols_9_80_planted.json", [entry_fourlist(9, 80, 9, True, 40, 16, state)], "oracle.fourlist")
     if args.only == "9_80":
         state = args.state or os.path.join(HERE, "sols_9_80.state.json")
         write("sols_9_80.json", [entry_fourlist(9, 80, SEED_9_80, False, None, 16, state)],

@@ -312,6 +312,11 @@ def test_config_9_80_planted_properties_and_subcube(msp):
     rng = np.random.default_rng(9)
     cols = sorted(int(c) for c in rng.choice(80, 34, replace=False))
     _subcube_parity(sols, A, d, cols, [int(x[c]) for c in cols])
+    # the four-list oracle's full solution set of the same instance, when stored
+    if os.path.exists(os.path.join(GOLDEN, "sols_9_80_planted.json")):
+        (e, A2, d2, x2, want), = load_golden("sols_9_80_planted.json")
+        assert np.array_equal(A2, A) and np.array_equal(d2, d)
+        assert sols == want
 
 
 def test_row_and_column_permutation_invariance(msp):
