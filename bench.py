@@ -123,7 +123,7 @@ def allreduce_sum(pg, x: float) -> float:
     return float(t.item())
 
 
-def oracle_sample(A, d, div=SAMPLE_DIV):
+def oracle_sample(A, d, div=SAMPLE_DIV, seed=SEED):
     """The four-list CPU oracle on the whole instance, timed over the first
     1/div of its residue slices (its inner lists are built in full), with
     the time of every slice projected from the records it enumerated:
@@ -142,7 +142,7 @@ def oracle_sample(A, d, div=SAMPLE_DIV):
     done = max(1, rl + rr)
     projected = tm["build"] + tm["join"] * total / done
     cores = os.cpu_count() or 1
-    sample = (f"the ({m},{n}) instance of seed {SEED} itself: four-list CPU oracle (OpenMP, {cores} threads) "
+    sample = (f"the ({m},{n}) instance of seed {seed} itself: four-list CPU oracle (OpenMP, {cores} threads) "
               f"with its inner lists built in full ({tm['build']:.2f} s) and residue slices [0, {hi}) of "
               f"{S} joined ({tm['join']:.2f} s, {done} of {total} half-subset records, {len(sols)} "
               f"solutions there); time to all solutions projected by records: {projected:.0f} s")

@@ -61,3 +61,19 @@ def test_committed_traffic_entries_name_existing_sources():
     for name, k in t["kernels"].items():
         assert os.path.exists(os.path.join(ROOT, k["source"])), name
         assert os.path.exists(os.path.join(ROOT, "profiles", k["case"])), name
+
+
+def test_oracle_sample_projects_the_whole_instance():
+    # the CPU baseline times the four-list oracle on a bounded slice range of
+    # the same instance and projects the time to all solutions by records
+    import bench
+    import msp_instances as mi
+    A, d, _ = mi.generate(4, 40, 3)
+    o = bench.oracle_sample(A, d, div=8, seed=3)
+    assert o["records_total"] == 2 * (1 << 20)
+    assert 0 < o["records"] < o["records_total"]
+    lo, hi, S = o["slices"]
+    assert lo == 0 and hi == max(1, S // 8)
+    assert o["projected_s"] >= o["build_s"]
+    assert abs(o["projected_s"] - (o["build_s"] + o["join_s"] * o["records_total"] / o["records"])) < 1e-9
+    assert "seed 3 " in o["sample"] and str(o["cores"]) in o["sample"]
