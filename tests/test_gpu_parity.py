@@ -486,6 +486,12 @@ def test_streaming_pass_with_large_inner_quarters(msp):
         xs = sum(1 << j for j, c in enumerate(free) if x[c])
         assert (xs,) in got or (xs & ((1 << 64) - 1), xs >> 64) in got
         assert solve(msp, A2, d2.astype(np.int32), {"direct": 1})[0] == want
+        # the shape of the default (10,90) plan: 2^25 classes, inner quarters
+        # of 29 columns (2^29-entry lists)
+        plan = {"class_bits": 25, "digit_bits": 0, "inner_bits": 4, "direct": 0}
+        got, st = solve(msp, A2, d2.astype(np.int32), plan)
+        assert st["class_bits"] == 25 and max(st["quarter"][2], st["quarter"][3]) == 29
+        assert got == want
 
 
 def test_streaming_pass_with_many_classes(msp):
