@@ -5,7 +5,7 @@
 // consecutive keys of their inner buckets) and hands them, four per lane at a
 // time, to the table code:
 //   left keys set a bit of a shared filter and take a slot of their home
-//   bucket (8 slots) through a 16-bit counter, moving on to later buckets
+//   bucket (8 slots) through its counter, moving on to later buckets
 //   through a per-warp queue when it is full;
 //   after a block barrier, right keys test the filter, and the few that pass
 //   (about 6 %) are looked up in the buckets through the queue; a matched
@@ -29,13 +29,13 @@ constexpr int kQueue = 64;  // deferred keys per warp
 
 // Shared join structures of a block, for a table of 2^TB slots:
 //   T     2^TB key slots in buckets of 8 (bucket = top TB - 3 key bits);
-//   C     one 16-bit fill counter per bucket, two per word;
+//   C     one 32-bit fill counter per bucket;
 //   F     a filter of 2^(TB + 3) bits (bit = top TB + 3 key bits) set for
 //         every left key, so that most right keys are settled by one load;
 //   claim one bit per slot: the slot's key was already reported.
 // T is never cleared: a bucket's slots past its counter are not read.
 __host__ __device__ constexpr uint32_t tab_words(int TB) { return 1u << TB; }
-__host__ __device__ constexpr uint32_t cnt_words(int TB) { return 1u << (TB - 4); }
+__host__ __device__ constexpr uint32_t cnt_words(int TB) { return 1u << (TB - 3); }
 __host__ __device__ constexpr uint32_t filt_words(int TB) { return 1u << (TB - 2); }
 __host__ __device__ constexpr uint32_t claim_words(int TB) { return 1u << (TB - 5); }
 
@@ -206,12 +206,9 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
   uint32_t *const q_w = wq + wp * kQueue;
   const uint32_t ltmask = (1u << ln) - 1u;
   uint32_t qn = 0;  // deferred keys of this warp (warp-uniform)
-  // Count-claimed slot: the previous fill of bucket b (one 16-bit counter).
-  auto take_slot = [&](uint32_t b) -> uint32_t {
-    const uint32_t sh = (b & 1u) << 4;
-    return (atomicAdd(C + (b >> 1), 1u << sh) >> sh) & 0xffffu;
-  };
-  auto count_of = [&](uint32_t b) -> uint32_t { return (C[b >> 1] >> ((b & 1u) << 4)) & 0xffffu; };
+  // Count-claimed slot: the previous fill of bucket b.
+  auto take_slot = [&](uint32_t b) -> uint32_t { return atomicAdd(C + b, 1u); };
+  auto count_of = [&](uint32_t b) -> uint32_t { return C[b]; };
   // A left key goes to the first slot its counter hands out; a key that
   // finds its bucket full moves on to the next bucket (counting it there
   // too), so a bucket whose counter passed 8 sends probes on as well.
