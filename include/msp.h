@@ -34,6 +34,10 @@
  *   - Limits: 1 <= m <= 16, 1 <= n <= 100, a_ij >= 0, d_i >= 0 and every row
  *     sum sum_j a_ij < 65536 (16-bit packed fields).  A right-hand side above
  *     its row sum is accepted and yields no solution.
+ *   - libmsp_checked.so (the MSP_CHECKED build) exports the same ABI; its
+ *     kernels test their data-dependent indices before each access, skip an
+ *     access that fails, and the solve then returns MSP_ECUDA naming the
+ *     check (msp_version() names the build).
  */
 #ifndef MSP_H
 #define MSP_H
