@@ -473,6 +473,7 @@ int run_direct(const std::vector<DirectLists> &lists, const DirectPlan &dp, uint
   // within a few launches; other solves queue every launch at once.
   constexpr uint32_t kInFlight = 2;
   EventRing ring(cancel ? kInFlight : 0);
+  CK(ring.status);
   for (uint32_t li = 0; li < nlaunch; ++li) {
     if (cancel) {
       if (li >= kInFlight) CK(ring.wait(li % kInFlight));

@@ -120,8 +120,12 @@ struct Prof {
 // i + size.
 struct EventRing {
   std::vector<cudaEvent_t> ev;
+  cudaError_t status = cudaSuccess;  // the first failed event creation, if any
   explicit EventRing(uint32_t n) : ev(n, nullptr) {
-    for (auto &e : ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    for (auto &e : ev) {
+      const cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      if (r != cudaSuccess && status == cudaSuccess) status = r;
+    }
   }
   ~EventRing() {
     for (auto e : ev)
