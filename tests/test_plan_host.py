@@ -78,3 +78,15 @@ def test_out_of_range(m, n):
 def test_null_output_is_rejected():
     lib = msp.load_library()
     assert lib.msp_plan(4, 30, ctypes.POINTER(msp.msp.PlanInfo)()) == -1
+
+
+def test_large_plans_fit_the_device():
+    # the streaming plans of the largest shapes keep their lists and per-class
+    # tables well inside a GB300's memory, leaving room for the pass buffers
+    for m, n, B, inner in [(10, 90, 25, 29), (11, 100, 27, 30)]:
+        p = msp.plan_info(m, n)
+        assert p["path"] == "streaming" and p["class_bits"] == B
+        assert max(p["quarter"][2], p["quarter"][3]) == inner
+        assert p["digit_bits"] == max(0, (max(p["quarter"][0] + p["quarter"][2],
+                                               p["quarter"][1] + p["quarter"][3])) - B - 12)
+        assert p["device_bytes"] < 150 << 30
