@@ -494,6 +494,21 @@ def test_streaming_pass_with_large_inner_quarters(msp):
         assert got == want
 
 
+@pytest.mark.slow
+def test_streaming_pass_with_the_n100_plan_shape(msp):
+    # the shape of the default (11,100) plan: 2^27 classes and inner quarters
+    # of 30 columns (2^30-entry lists, about 120 GB), exact class sizes summed
+    # over the outer elements, on the (10,70) restriction of the planted
+    # (10,90) instance against the oracle's full set
+    for e, A, d, x, _ in load_golden("sols_10_70_subcube.json"):
+        A2, d2, free = mi.restrict(A, d, e["fixed_cols"], e["fixed_vals"])
+        want = [tuple(int(w, 16) for w in s) for s in e["solutions_restricted"]]
+        plan = {"class_bits": 27, "digit_bits": 0, "inner_bits": 4, "direct": 0}
+        got, st = solve(msp, A2, d2.astype(np.int32), plan)
+        assert st["class_bits"] == 27 and max(st["quarter"][2], st["quarter"][3]) == 30
+        assert got == want
+
+
 def test_streaming_pass_with_many_classes(msp):
     # the plans of n >= 96 take up to 2^27 residue classes, whose exact sizes
     # come from the outer elements (fewer than the classes); forced here on
