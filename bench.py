@@ -344,6 +344,10 @@ def native(args, world, rank, local, pg):
         roof["traffic"] = traffic_per_launch(roof["kernel"], roof["bytes_per_launch"])
         # the HBM fraction is low by design (no record reaches device memory):
         # the on-chip limits of the same kernel source, from ncu
+        # the join's own rate: every half-pair record of a step joined in its time
+        if roof["kernel"] == "direct" and dom[1]["ms"] > 0:
+            recs = (st0["records_left"] + st0["records_right"]) * args.steps
+            roof["records_per_s"] = recs / (dom[1]["ms"] / 1000.0)
         cap = _capture(roof["kernel"])
         if cap is not None and "onchip" in cap:
             roof["onchip"] = dict(cap["onchip"], source="ncu, profiles/" + cap["onchip"]["case"])
