@@ -14,6 +14,13 @@ With N > 1 (torchrun) every rank solves its own instance (seed + rank): the
 units are independent, so there is no data-path collective ("weak"
 scaling); value = candidate pairs of all ranks / the slowest rank's time.
 
+The default run (rank 0, one GPU) then adds a ``secondary`` block with short
+runs of the other configurations (``--no-secondary`` skips it): the (10,90)
+1/64 part with its projected full time, the served mixed stream against
+sequential solving (p50/p99, 256 requests at the sequential service rate),
+the batch of 64 (6,50) instances, time to the first solution over four
+planted (9,80) instances and the (11,100,50) 1/4096 part.
+
 ``--impl reference`` times the CPU oracle (the four-list meet in the middle
 over residue slices) on a bounded sample of the same instance: its lists are
 built in full and 1/2048 of its slices joined, and the time to all solutions
@@ -55,6 +62,8 @@ def parse():
     ap.add_argument("--rows", "--m", dest="m", type=int, default=M_)
     ap.add_argument("--cols", "--n", dest="n", type=int, default=N_)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default workload: skip the short runs of the other configurations")
     ap.add_argument("--config", choices=["9_80", "batch_6_50", "serving", "10_90_part", "profile_part",
                                          "profile_small", "first_9_80", "k_sweep", "first_10_90",
                                          "11_100_part"],
@@ -305,7 +314,7 @@ def native(args, world, rank, local, pg):
     # end to end through the public API: host buffers in, solutions out
     e2e_ms = []
     h2d = d2h = 0
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, 3)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with msp.Instance(A, d) as e_inst:
@@ -381,6 +390,8 @@ def native(args, world, rank, local, pg):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if rank == 0 and world == 1 and not args.no_secondary:
+        out["secondary"] = secondary(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = run_cpu_baseline(A, d, cand)
         out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "projected_s")}
@@ -424,7 +435,13 @@ def _emit(obj):
     print(json.dumps(obj), flush=True)
 
 
-def bench_batch(args):
+def _done(emit, obj):
+    if emit:
+        _emit(obj)
+    return obj
+
+
+def bench_batch(args, emit=True):
     import paper_2507_05045_gb300 as msp
     from paper_2507_05045_gb300 import build
     build.build()
@@ -450,7 +467,7 @@ def bench_batch(args):
     assert rst == rb
     h2d = sum(A.nbytes + d.nbytes for A, d in pairs)
     d2h = sum(len(r) * 8 for r in rb)
-    _emit({"metric": "instances/s, 64 (6,50) instances per batched call", "value": 64 / tb,
+    return _done(emit, {"metric": "instances/s, 64 (6,50) instances per batched call", "value": 64 / tb,
            "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "u64", "data": "synthetic",
@@ -484,7 +501,7 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, int(round(q / 100.0 * (len(xs) - 1))))]
 
 
-def bench_serving(args):
+def bench_serving(args, emit=True):
     import threading
     import paper_2507_05045_gb300 as msp
     from paper_2507_05045_gb300 import build
@@ -570,10 +587,10 @@ def bench_serving(args):
            "e2e": {"value": len(reqs) / span_s, "unit": "requests/s",
                    "h2d_bytes_per_step": int(sum(A.nbytes + d.nbytes for A, d in reqs)),
                    "d2h_bytes_per_step": int(sum(len(r) * 8 for r in res_s))}}
-    _emit(out)
+    return _done(emit, out)
 
 
-def _bench_part(args, m, n, seed, part, K=100):
+def _bench_part(args, m, n, seed, part, K=100, emit=True):
     """One plain (m, n) instance over a fixed 1/part[1] of its residue
     classes; the full time is projected from the records joined: the list
     build once, the rest of the part's time scaled by all records / records
@@ -596,7 +613,7 @@ def _bench_part(args, m, n, seed, part, K=100):
     once_s = sum(st["kernels"].get(k, {}).get("ms", 0.0) for k in ("gray", "bucket", "c1")) / 1000.0
     proj = once_s + (dt - once_s) * total / st["records_done"]
     c1 = st["row1_candidates"]
-    _emit({"metric": f"candidate pairs/s at ({m},{n}) over a seeded 1/{part[1]} of the residue classes "
+    return _done(emit, {"metric": f"candidate pairs/s at ({m},{n}) over a seeded 1/{part[1]} of the residue classes "
                      "(projected full time)", "value": c1 / proj, "unit": "candidate pairs/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
@@ -610,15 +627,15 @@ def _bench_part(args, m, n, seed, part, K=100):
            "kernels": st["kernels"]})
 
 
-def bench_10_90(args):
+def bench_10_90(args, emit=True):
     # fixed, seeded choice of one 1/64 of the residue classes
-    _bench_part(args, 10, 90, 1090, (37, 64))
+    return _bench_part(args, 10, 90, 1090, (37, 64), emit=emit)
 
 
-def bench_11_100(args):
+def bench_11_100(args, emit=True):
     # the paper's (11,100,50) class: coefficients in [0, 50); a fixed, seeded
     # 1/4096 of the 2^26 residue classes of the n >= 96 streaming plan
-    _bench_part(args, 11, 100, 11100, (2731, 4096), K=50)
+    return _bench_part(args, 11, 100, 11100, (2731, 4096), K=50, emit=emit)
 
 
 def bench_profile_part(args):
@@ -660,7 +677,7 @@ def bench_profile_small(args):
            "solutions": len(sols), "records_done": st["records_done"], "kernels": st["kernels"]})
 
 
-def bench_first(args):
+def bench_first(args, emit=True):
     """Time to the first solution (the paper's Algorithm 2 returns the first
     x; its Table 1 times are most likely time to first), on the direct pass:
     the plain bench instance (7 solutions) and, averaged like the paper's,
@@ -686,7 +703,7 @@ def bench_first(args):
                      "solutions_found": len(sols), "classes_done": st["classes_done"],
                      "classes_total": st["classes_total"]})
     planted = [r["time_to_first_s"] for r in rows[1:]]
-    _emit({"metric": "time to first solution at (9,80)", "value": rows[0]["time_to_first_s"], "unit": "s",
+    return _done(emit, {"metric": "time to first solution at (9,80)", "value": rows[0]["time_to_first_s"], "unit": "s",
            "planted_average_s": float(np.mean(planted)) if planted else None,
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
            "dtype": "u32", "data": "synthetic",
@@ -759,6 +776,47 @@ def bench_k_sweep(args):
            "warmup": args.warmup, "higher_is_better": False, "dtype": "u32", "data": "synthetic",
            "config": {"workload": "plain (8,70) seed 8 and (9,80) seed 9080, a_ij in [0, K), K = 50, 100, 200"},
            "classes": rows})
+
+
+def _with(args, **kw):
+    a = argparse.Namespace(**vars(args))
+    for k, v in kw.items():
+        setattr(a, k, v)
+    return a
+
+
+def secondary(args):
+    """Short runs of the other configurations, after the headline's timed
+    region (each in its own try, so that one failure leaves the line): the
+    (10,90) 1/64 part and its projection, the served mixed stream against
+    sequential solving (p50/p99), the batch of 64 (6,50) instances, time to
+    the first solution over four planted (9,80) instances and the
+    (11,100,50) 1/4096 part."""
+    runs = {
+        "10_90_part": lambda: bench_10_90(_with(args, steps=1, warmup=0), emit=False),
+        "serving": lambda: bench_serving(_with(args, requests=256, rate_factor=1.0), emit=False),
+        "batch_6_50": lambda: bench_batch(_with(args, steps=3, warmup=2), emit=False),
+        "first_9_80": lambda: bench_first(_with(args, steps=1, warmup=0, instances=4), emit=False),
+        "11_100_part": lambda: bench_11_100(_with(args, steps=1, warmup=0), emit=False),
+    }
+    keep = {
+        "10_90_part": ("metric", "ms_per_step", "projected_full_time_s", "list_build_s", "records_done",
+                       "records_total", "config"),
+        "serving": ("value", "unit", "served", "sequential", "results_identical", "config"),
+        "batch_6_50": ("value", "unit", "ms_per_step", "sequential", "streaming_batch", "speedup_vs_sequential"),
+        "first_9_80": ("value", "planted_average_s", "instances", "paper"),
+        "11_100_part": ("metric", "ms_per_step", "projected_full_time_s", "list_build_s", "config"),
+    }
+    out = {}
+    for name, run in runs.items():
+        t0 = time.perf_counter()
+        try:
+            r = run()
+            out[name] = {k: r[k] for k in keep[name] if k in r}
+        except Exception as e:  # reported in the line, the headline stands
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def main():

@@ -77,3 +77,37 @@ def test_oracle_sample_projects_the_whole_instance():
     assert o["projected_s"] >= o["build_s"]
     assert abs(o["projected_s"] - (o["build_s"] + o["join_s"] * o["records_total"] / o["records"])) < 1e-9
     assert "seed 3 " in o["sample"] and str(o["cores"]) in o["sample"]
+
+
+def test_secondary_block_reports_each_run_and_survives_a_failure(monkeypatch):
+    import bench
+    args = bench.argparse.Namespace(steps=20, warmup=3, requests=512, rate_factor=0.8, instances=4)
+    seen = {}
+
+    def fake(name, fail=False):
+        def run(a, emit=True):
+            assert emit is False
+            seen[name] = a
+            if fail:
+                raise RuntimeError("no device")
+            return {"value": 1.0, "unit": "u", "ms_per_step": 2.0, "projected_full_time_s": 3.0,
+                    "metric": "m", "config": {}, "served": {}, "sequential": {}, "results_identical": True,
+                    "planted_average_s": 4.0, "instances": [], "paper": "p", "unused": 0}
+        return run
+
+    monkeypatch.setattr(bench, "bench_10_90", fake("10_90"))
+    monkeypatch.setattr(bench, "bench_serving", fake("serving", fail=True))
+    monkeypatch.setattr(bench, "bench_batch", fake("batch"))
+    monkeypatch.setattr(bench, "bench_first", fake("first"))
+    monkeypatch.setattr(bench, "bench_11_100", fake("11_100"))
+    out = bench.secondary(args)
+    assert set(out) == {"10_90_part", "serving", "batch_6_50", "first_9_80", "11_100_part"}
+    assert out["serving"]["error"] == "RuntimeError: no device"
+    assert out["10_90_part"]["projected_full_time_s"] == 3.0 and "unused" not in out["10_90_part"]
+    assert all("wall_s" in v for v in out.values())
+    # short forms: one step, a 256-request stream at the service rate; the
+    # caller's own arguments are left as they were
+    assert seen["10_90"].steps == 1 and seen["10_90"].warmup == 0
+    assert seen["serving"].requests == 256 and seen["serving"].rate_factor == 1.0
+    assert seen["first"].instances == 4
+    assert args.steps == 20 and args.requests == 512
