@@ -107,7 +107,7 @@ def test_secondary_block_reports_each_run_and_survives_a_failure(monkeypatch):
     assert all("wall_s" in v for v in out.values())
     # short forms: one step, a 256-request stream at the service rate; the
     # caller's own arguments are left as they were
-    assert seen["10_90"].steps == 1 and seen["10_90"].warmup == 0
+    assert seen["10_90"].steps == 1 and seen["10_90"].warmup == 1
     assert seen["serving"].requests == 256 and seen["serving"].rate_factor == 1.0
     assert seen["first"].instances == 4
     assert args.steps == 20 and args.requests == 512
