@@ -715,8 +715,8 @@ __device__ __forceinline__ void emit(const FastPass &p, bool e, uint64_t key, ui
 }
 
 // Bucket and fingerprint of a key: the kJBits bits below the top D (digit)
-// bits, then 16 more; fingerprint 0 marks an empty slot, so a key whose 16
-// bits are 0 uses 1.
+// bits, then 16 more (a key whose 16 bits are 0 uses 1, so that a slot of
+// the zeroed table never matches).
 template <int D>
 __device__ __forceinline__ uint32_t jbucket(uint64_t key) {
   return static_cast<uint32_t>(key >> (64 - D - kJBits)) & (kJBuckets - 1u);
@@ -739,6 +739,9 @@ __device__ __forceinline__ bool probe(uint64_t key, const uint64_t *__restrict__
                                       uint32_t n_ovf, uint32_t *flags) {
   const uint32_t b = jbucket<D>(key);
   const uint32_t fp = jfp<D>(key);
+  // all 8 slots are compared at once; slots past the count hold stale
+  // fingerprints of earlier partitions, so a hit is confirmed below on the
+  // counted slots only
   const uint4 w = *reinterpret_cast<const uint4 *>(fps + b * kJSlots);
   const uint32_t f2 = fp * 0x00010001u;
   const uint32_t any = zero_half(w.x ^ f2) | zero_half(w.y ^ f2) | zero_half(w.z ^ f2) | zero_half(w.w ^ f2);
@@ -781,6 +784,10 @@ __global__ void __launch_bounds__(kJT, 2) join_fast_kernel(FastPass p, int nseg)
   __shared__ __align__(8) uint64_t barCheck;
   __shared__ uint32_t s_novf;
   __shared__ int s_ok;
+  // the partition of this iteration and of the next: thread 0 resolves the
+  // next one when it issues its left keys, so the dependent loads of
+  // seg_ref leave the critical path of the iteration
+  __shared__ SegRef s_ref[2];
   if (threadIdx.x == 0) {
     mbar_init(&barL, 1);
     mbar_init(&barCheck, 1);
@@ -802,11 +809,13 @@ __global__ void __launch_bounds__(kJT, 2) join_fast_kernel(FastPass p, int nseg)
   int s = blockIdx.x;
   if (s < nseg && threadIdx.x == 0) {
     const SegRef r0 = seg_ref(p, s);
+    s_ref[0] = r0;
     issue_keys(r0.L, r0.nL, bufL, &barL);
   }
+  __syncthreads();
   uint32_t phL = 0;
-  for (; s < nseg; s += G) {
-    const SegRef r = seg_ref(p, s);
+  for (uint32_t it = 0; s < nseg; s += G, ++it) {
+    const SegRef r = s_ref[it & 1u];
     // right keys of this partition: coalesced 128-bit loads into registers,
     // in flight while the left side is hashed
     ulonglong2 rk[kJPairs];
@@ -838,6 +847,7 @@ __global__ void __launch_bounds__(kJT, 2) join_fast_kernel(FastPass p, int nseg)
     if (sn < nseg && threadIdx.x == 0) {
       fence_proxy_async();
       const SegRef rn = seg_ref(p, sn);
+      s_ref[(it + 1u) & 1u] = rn;  // read after the barrier that ends this iteration
       issue_keys(rn.L, rn.nL, bufL, &barL);
     }
     const uint32_t n_ovf = s_novf;
@@ -861,7 +871,8 @@ __global__ void __launch_bounds__(kJT, 2) join_fast_kernel(FastPass p, int nseg)
     __syncthreads();
     for (int i = threadIdx.x; i < kJBuckets; i += kJT) cnt[i] = 0;
     for (int i = threadIdx.x; i < nflag; i += kJT) flags[i] = 0;
-    for (int i = threadIdx.x; i < nfp16; i += kJT) reinterpret_cast<uint4 *>(fps)[i] = make_uint4(0, 0, 0, 0);
+    // the fingerprints are not cleared: slots past a bucket's count are
+    // stale, and probe() confirms a fingerprint hit only on counted slots
     if (threadIdx.x == 0) s_novf = 0;
     // the next wait_phase begins with a block barrier
   }
