@@ -179,10 +179,10 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
   uint32_t *const wq = wbb + kDW * 32;      // [kDW][kQueue]
   uint32_t *const wtot = wq + kDW * kQueue;
   const int noL = p.no[0], noR = p.no[1];
-  // per-class totals, double-buffered by class parity: class i accumulates
-  // into slot i & 1 before its first barrier, and the other slot is reset
-  // after that barrier, once every thread has read it for class i - 1
-  __shared__ unsigned long long s_fill[2][2];
+  // each warp's record totals of a class (left, right), double-buffered by
+  // class parity: class i writes slot i & 1 before its first barrier and
+  // every warp sums the slot after it, with no shared atomics
+  __shared__ uint2 s_wsum[2][kDW];
   __shared__ uint32_t s_bad[2];
   __shared__ uint32_t s_item;
   __shared__ DirectInst s_inst;
@@ -197,7 +197,6 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
   };
   clear_table();
   if (threadIdx.x < 2) {
-    s_fill[threadIdx.x][0] = s_fill[threadIdx.x][1] = 0;
     s_bad[threadIdx.x] = 0;
   }
   uint2 *const et_w = et + wp * 32;
@@ -340,26 +339,32 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
       // ---- bucket of this warp's outer subsets (lane = subset) ----
       load_bounds(r, ri > rb);
       const uint32_t stL = pfL0, lnL = pfL1 - pfL0, stR = pfR0, lnR = pfR1 - pfR0;
-      unsigned long long sumL = lnL, sumR = lnR;
-      bool big = lnL >= (1u << 24) || lnR >= (1u << 24);
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        sumL += __shfl_xor_sync(kFull, sumL, o);
-        sumR += __shfl_xor_sync(kFull, sumR, o);
-      }
-      big = __any_sync(kFull, big);
+      const bool big = __any_sync(kFull, lnL >= (1u << 24) || lnR >= (1u << 24));
+      // a warp's 32 buckets, each clamped to 2^24 (a larger one skips the
+      // class), stay below 2^29 records
+      const uint32_t sumL = __reduce_add_sync(kFull, min(lnL, 1u << 24));
+      const uint32_t sumR = __reduce_add_sync(kFull, min(lnR, 1u << 24));
       if (ln == 0) {
-        atomicAdd(&s_fill[par][0], sumL);
-        atomicAdd(&s_fill[par][1], sumR);
-        wtot[wp] = static_cast<uint32_t>(min(sumL, 0xffffffffull));
+        s_wsum[par][wp] = make_uint2(sumL, sumR);
+        wtot[wp] = sumL;
         if (big) {
           atomicOr(&s_bad[par], 1u);
           atomicOr(p.error, 1u);
         }
       }
       __syncthreads();
-      const unsigned long long TL = s_fill[par][0];
-      const unsigned long long TR = s_fill[par][1];
+      // class totals: lane w < kDW takes warp w's totals
+      unsigned long long TL = 0, TR = 0;
+      if (ln < static_cast<uint32_t>(kDW)) {
+        const uint2 t = s_wsum[par][ln];
+        TL = t.x;
+        TR = t.y;
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        TL += __shfl_xor_sync(kFull, TL, o);
+        TR += __shfl_xor_sync(kFull, TR, o);
+      }
       // a class past 2^31 records on a side, or a bucket past 2^24, is beyond
       // this kernel: it is skipped and the host, seeing the error flag, solves
       // the instance on another path
@@ -367,7 +372,6 @@ __global__ void __launch_bounds__(kDT, 2) direct_join_kernel(DirectPass p) {
       if (skip && threadIdx.x == 0) atomicOr(p.error, 1u);
       if (threadIdx.x == 0) {
         my_records += TL + TR;
-        s_fill[par ^ 1u][0] = s_fill[par ^ 1u][1] = 0;
         s_bad[par ^ 1u] = 0;
       }
       const uint32_t cap = p.insert_cap;
