@@ -38,8 +38,12 @@ __device__ __forceinline__ uint32_t digit_t(uint64_t key) {
   }
 }
 
+// Block-wide exclusive scan of one value per thread; *total is the block's
+// sum.  One block barrier: every warp scans the warp totals itself.  With
+// reuse a second barrier follows, so that the next call may overwrite wt;
+// a caller that passes a block barrier before its next call passes false.
 template <typename T>
-__device__ T scan_excl(T v, T *wt, T *total) {
+__device__ T scan_excl(T v, T *wt, T *total, bool reuse) {
   const int ln = lane(), wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   T x = v;
 #pragma unroll
@@ -49,20 +53,17 @@ __device__ T scan_excl(T v, T *wt, T *total) {
   }
   if (ln == 31) wt[wp] = x;
   __syncthreads();
-  if (wp == 0) {
-    T t = ln < nw ? wt[ln] : T(0);
+  T t = ln < nw ? wt[ln] : T(0);
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      T y = __shfl_up_sync(0xffffffffu, t, o);
-      if (ln >= o) t += y;
-    }
-    if (ln < nw) wt[ln] = t;
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, t, o);
+    if (ln >= o) t += y;
   }
-  __syncthreads();
-  const T before = wp ? wt[wp - 1] : T(0);
-  *total = wt[nw - 1];
-  __syncthreads();
-  return x + before - v;
+  // wp is warp-uniform: every lane reads the same source lane
+  const T b = __shfl_sync(0xffffffffu, t, wp > 0 ? wp - 1 : 0);
+  *total = __shfl_sync(0xffffffffu, t, nw - 1);
+  if (reuse) __syncthreads();
+  return x + (wp > 0 ? b : T(0)) - v;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -388,7 +389,10 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
         const uint32_t c = cnt[e];
         const uint32_t cc = min(c, static_cast<uint32_t>(kScRound + 1));
         uint32_t tot_packed;
-        const uint32_t ex = scan_excl<uint32_t>((cc << 10) | (c ? 1u : 0u), s_wt, &tot_packed);
+        // a further slice scans again; after the last one the block
+        // barrier below comes first
+        const uint32_t ex = scan_excl<uint32_t>((cc << 10) | (c ? 1u : 0u), s_wt, &tot_packed,
+                                                (e + 1) * kScT < w_n);
         if (c) {
           const int idx = e * kScT + threadIdx.x;
           const unsigned long long pre = rec_carry + (ex >> 10);
@@ -493,7 +497,7 @@ __global__ void __launch_bounds__(kScT, 1024 / kScT) scatter_fast_kernel(FastPas
 #pragma unroll
         for (int q = 0; q < pd; ++q) bv[q] = hv[q] ? atomicAdd(fill + threadIdx.x * pd + q, hv[q]) : 0u;
         uint32_t htot;
-        uint32_t o = scan_excl<uint32_t>(hsum, s_wt, &htot);
+        uint32_t o = scan_excl<uint32_t>(hsum, s_wt, &htot, false);  // a block barrier follows
 #pragma unroll
         for (int q = 0; q < pd; ++q) {
           const int gd = threadIdx.x * pd + q;
