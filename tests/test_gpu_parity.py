@@ -544,6 +544,23 @@ def test_first_solution_mode_streaming_pass(msp):
             assert got and set(got) <= set(sols)
 
 
+@pytest.mark.slow
+def test_config_10_90_full_size_first_solution(msp):
+    # the (10,90) configuration at full size on the streaming pass (2^25
+    # classes, 29-column inner quarters, lists of about 17 GB): a planted
+    # instance whose first solution lies in the first few percent of the
+    # classes (seed 1093, x* with 45 ones) stops early, and every solution it
+    # reports solves A x = d exactly
+    A, d, x = mi.generate(10, 90, 1093, planted=True, h=45)
+    with msp.Instance(A, d, first=True) as inst:
+        got = inst.solve_all()
+        st = inst.stats()
+    assert st["path"] == "streaming" and st["class_bits"] == 25
+    assert got
+    _check_solutions_exact(A, d, got)
+    assert 0 < st["classes_done"] < st["classes_total"]
+
+
 def test_first_solution_mode(msp):
     # time-to-first: a nonempty subset of the oracle's full solution set,
     # found before all classes are joined; an instance without solutions is
