@@ -607,19 +607,22 @@ cudaError_t launch_scatter_fast(const FastPass &p, int nclass_run, cudaStream_t 
 }
 
 // -------------------------------------------------------------------------
-// Join (S4 second digit + S5).  Persistent, one block of 1024 threads per SM.
-// Partition s = (class, digit).  The left keys arrive by cp.async.bulk into
-// a shared buffer one partition ahead and are hashed into a shared table of
-// 4096 buckets (the 12 key bits below the digit) with 8 slots each; a slot
-// holds an 18-bit fingerprint (the next key bits) and the key's index in the
-// partition, a bucket past 8 keys spills into a short overflow list.  The
-// right keys are read straight from device memory with coalesced 128-bit
-// loads into registers (each is used once) and probe their bucket: one
-// 128-bit shared load and four fingerprint compares for most buckets.  A
-// fingerprint hit is confirmed against the full left key in device memory;
-// the smallest index of an equal left key is claimed with a shared bit (so
-// duplicate right keys emit once) and the (class, key) pair is appended
-// with one atomic per warp.
+// Join (S4 second digit + S5).  Persistent, two blocks of 512 threads per
+// SM.  Partition s = (class, digit).  Thread 0 resolves the next
+// partition's descriptor (where its keys lie, how many) and starts its left
+// keys by cp.async.bulk into a shared buffer one partition ahead.  The left
+// keys are hashed into a shared table of 2048 buckets (the 11 key bits below
+// the digit) with 8 slots each; a slot holds a 16-bit fingerprint (the next
+// key bits) and the key's 16-bit index in the partition, and a bucket past 8
+// keys spills into a short overflow list.  Only the bucket counts are
+// cleared between partitions: slots past a count are stale and never
+// confirmed.  The right keys are read straight from device memory with
+// coalesced 128-bit loads into registers (each is used once) and probe their
+// bucket: one 128-bit shared load and four fingerprint compares for most
+// buckets.  A fingerprint hit is confirmed against the full left key in
+// device memory; the smallest index of an equal left key is claimed with a
+// shared bit (so duplicate right keys emit once) and the (class, key) pair
+// is appended with one atomic per warp.
 // -------------------------------------------------------------------------
 constexpr int kJT = 512;                    // threads per block, two blocks per SM
 constexpr int kJBits = 11;                  // buckets of the probe table
