@@ -299,17 +299,12 @@ __global__ void __launch_bounds__(kVT) direct_verify_kernel(DirectVerify v) {
   static_assert(kVT >= kOuterMax, "one pass over the outer subsets");
   __shared__ uint2 cand[2][kVCand];
   __shared__ uint32_t ncand[2];
-  __shared__ uint64_t scol[2][kInnerMax][4];
   const uint32_t key = v.match_key[blockIdx.x];
   const uint32_t tagged = v.match_cls[blockIdx.x];
   const uint32_t ii = tagged >> v.class_bits;
   const uint32_t r = tagged & v.cmask;
   const DirectVerifyInst &vi = v.inst[ii];
   if (threadIdx.x < 2) ncand[threadIdx.x] = 0;
-  for (int i = threadIdx.x; i < 2 * kInnerMax * 4; i += kVT) {
-    const int s = i / (kInnerMax * 4), j = (i / 4) % kInnerMax, w = i % 4;
-    scol[s][j][w] = j < v.qi[s] ? vi.icol[s][j * 4 + w] : 0ull;
-  }
   __syncthreads();
   // thread a scans the bucket of outer subset a on both sides; the bucket
   // bounds of the two sides are loaded together
@@ -362,13 +357,15 @@ __global__ void __launch_bounds__(kVT) direct_verify_kernel(DirectVerify v) {
     uint64_t vec[4];
     for (int w = 0; w < 4; ++w) vec[w] = vi.ovec[0][l.x * 4 + w] + vi.ovec[1][rr.x * 4 + w];
     const uint32_t mL = vi.imask[0][l.y], mR = vi.imask[1][rr.y];
+    // the packed inner columns are read where a pair needs them (about one
+    // pair per match; the two column tables stay in cache)
     for (uint32_t b = mL; b; b &= b - 1) {
       const int j = __ffs(b) - 1;
-      for (int w = 0; w < 4; ++w) vec[w] += scol[0][j][w];
+      for (int w = 0; w < 4; ++w) vec[w] += __ldg(vi.icol[0] + j * 4 + w);
     }
     for (uint32_t b = mR; b; b &= b - 1) {
       const int j = __ffs(b) - 1;
-      for (int w = 0; w < 4; ++w) vec[w] += scol[1][j][w];
+      for (int w = 0; w < 4; ++w) vec[w] += __ldg(vi.icol[1] + j * 4 + w);
     }
     bool eq = true;
     for (int w = 0; w < v.W; ++w) eq &= vec[w] == vi.dvec[w];
