@@ -157,7 +157,9 @@ MSP_API int msp_set_memory_budget(msp_instance *inst, size_t bytes);
  *                        solved on the exact path)
  *   MSP_OPT_INNER_BITS   the inner quarter of each side (Q3 of L, Q4 of R)
  *                        gets B + value columns (at most 27, or 30 when B is
- *                        above 23; never fewer than the even split), so an
+ *                        above 23 or a half has 44 columns or more; never
+ *                        fewer than the even split; the formula takes 4, or 5
+ *                        for halves of 44 to 47 columns), so an
  *                        inner residue bucket holds
  *                        about 2^value elements: the run of records one outer
  *                        element expands to in the scatter, in [0, 12]

@@ -175,7 +175,10 @@ def autotune(m: int, n: int, A=None, d=None, sample_records: float = 2 ** 33, se
         st = inst.stats()
     q = st["quarter"]
     lg = max(q[0] + q[2], q[1] + q[3])
-    base = {"class_bits": st["class_bits"], "digit_bits": st["digit_bits"], "inner_bits": 4}
+    # the formula's inner buckets: 2^(inner columns - B) elements (the inner
+    # quarter may be capped below B + its target)
+    inner0 = max(0, max(q[2], q[3]) - st["class_bits"])
+    base = {"class_bits": st["class_bits"], "digit_bits": st["digit_bits"], "inner_bits": inner0}
     table = []
     best = None
     for plan in candidates(base, lg, direct_ok):

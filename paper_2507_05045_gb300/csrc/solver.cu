@@ -50,13 +50,15 @@ Plan make_plan(int m, int n, const PlanChoice &ch) {
   p.lgR = p.q[1] + p.q[3];
   const int lgmax = std::max(p.lgL, p.lgR);
   // about 2^21 records per class and side (at most 2^23 classes).  Halves
-  // of 44 columns or more take classes of about 2^20 records, up to 2^27 of
-  // them: fewer digits per class, so a scatter round (4096 records) puts
-  // more records into each partition and reserves fewer runs (measured on
-  // the (10,90) and (11,100) classes: 10 % and 23 % faster passes than
-  // 2^23 and 2^26 classes).
+  // of 44 to 47 columns keep classes of 2^21 records with inner buckets of
+  // about 32 elements (inner quarters of B + 5 columns), so a scatter window
+  // expands half as many outer elements per round (measured on the (10,90)
+  // class: 3.4 % faster passes than 2^25 classes of 2^20 records with
+  // buckets of 16).  Halves of 48 columns or more take classes of about
+  // 2^20 records, up to 2^27 of them: fewer digits per class (measured on
+  // the (11,100) class: 23 % faster than 2^26 classes).
   p.B = ch.B >= 0 ? std::min(kMaxStreamClassBits, ch.B) : std::min(23, std::max(0, lgmax - 21));
-  if (ch.B < 0 && lgmax >= 44) p.B = std::min(kMaxStreamClassBits, lgmax - 20);
+  if (ch.B < 0 && lgmax >= 44) p.B = std::min(kMaxStreamClassBits, lgmax >= 48 ? lgmax - 20 : lgmax - 21);
   // row 1 alone while its residues stay uniform (2^B <= 256 against a
   // row-1 spread of a few hundred); three rows beyond, which keeps the class
   // sizes within about one percent of each other (four rows past 2^18
@@ -65,13 +67,14 @@ Plan make_plan(int m, int n, const PlanChoice &ch) {
   p.t = std::min(p.t, m);
   // Uneven halves: the inner quarter of each side (Q3 of L, Q4 of R) takes
   // columns from the outer one until an inner residue bucket holds about 16
-  // elements (2^(q_inner - B)), at most 2^27 of them (2^30 for the plans of
-  // more than 2^23 classes, whose lists then take about 120 GB), so that
+  // elements (2^(q_inner - B); 32 for halves of 44 to 47 columns), at most
+  // 2^27 of them (2^30 for the plans of more than 2^23 classes or halves of
+  // 44 columns or more, whose lists then take up to about 120 GB), so that
   // every outer element of a scatter window expands to a run of consecutive
   // inner keys.  |L| and |R| do not change, nor do the classes and
   // partitions.
-  const int inner_bits = ch.inner >= 0 ? ch.inner : 4;
-  const int inner_cap = p.B > 23 ? 30 : 27;
+  const int inner_bits = ch.inner >= 0 ? ch.inner : (lgmax >= 44 && lgmax < 48 ? 5 : 4);
+  const int inner_cap = p.B > 23 || lgmax >= 44 ? 30 : 27;
   for (int side = 0; side < 2; ++side) {
     const int tot = p.q[side] + p.q[side + 2];
     const int want = std::min({std::max(p.q[side + 2], p.B + inner_bits), inner_cap, tot - 1});

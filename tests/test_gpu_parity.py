@@ -486,8 +486,13 @@ def test_streaming_pass_with_large_inner_quarters(msp):
         xs = sum(1 << j for j, c in enumerate(free) if x[c])
         assert (xs,) in got or (xs & ((1 << 64) - 1), xs >> 64) in got
         assert solve(msp, A2, d2.astype(np.int32), {"direct": 1})[0] == want
-        # the shape of the default (10,90) plan: 2^25 classes, inner quarters
-        # of 29 columns (2^29-entry lists)
+        # the shape of the default (10,90) plan: 2^24 classes, inner quarters
+        # of 29 columns (2^29-entry lists, buckets of about 32)
+        plan = {"class_bits": 24, "digit_bits": 0, "inner_bits": 5, "direct": 0}
+        got, st = solve(msp, A2, d2.astype(np.int32), plan)
+        assert st["class_bits"] == 24 and max(st["quarter"][2], st["quarter"][3]) == 29
+        assert got == want
+        # the shape of the earlier (10,90) plan: 2^25 classes, buckets of 16
         plan = {"class_bits": 25, "digit_bits": 0, "inner_bits": 4, "direct": 0}
         got, st = solve(msp, A2, d2.astype(np.int32), plan)
         assert st["class_bits"] == 25 and max(st["quarter"][2], st["quarter"][3]) == 29
@@ -546,7 +551,7 @@ def test_first_solution_mode_streaming_pass(msp):
 
 @pytest.mark.slow
 def test_config_10_90_full_size_first_solution(msp):
-    # the (10,90) configuration at full size on the streaming pass (2^25
+    # the (10,90) configuration at full size on the streaming pass (2^24
     # classes, 29-column inner quarters, lists of about 17 GB): a planted
     # instance whose first solution lies in the first few percent of the
     # classes (seed 1093, x* with 45 ones) stops early, and every solution it
@@ -555,7 +560,7 @@ def test_config_10_90_full_size_first_solution(msp):
     with msp.Instance(A, d, first=True) as inst:
         got = inst.solve_all()
         st = inst.stats()
-    assert st["path"] == "streaming" and st["class_bits"] == 25
+    assert st["path"] == "streaming" and st["class_bits"] == 24
     assert got
     _check_solutions_exact(A, d, got)
     assert 0 < st["classes_done"] < st["classes_total"]
